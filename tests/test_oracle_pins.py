@@ -1,0 +1,537 @@
+"""Pins for the FP64 oracle: every check compares it with something other than
+itself -- constants printed in the paper (tests/golden), closed forms,
+library routines (numpy eigh), exact permutations, invariances and brute
+force on tiny inputs -- so that a dropped term, a wrong sign, index or
+transposed operand in the oracle fails at least one of them.
+No GPU needed."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02398_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(key):
+    for line in open(os.path.join(GOLDEN, "paper_constants.txt")):
+        line = line.split("#", 1)[0].split()
+        if len(line) == 2 and line[0] == key:
+            return float(line[1])
+    raise KeyError(key)
+
+
+# ----------------------------------------------------------- closed forms --
+
+def sphere_moment(alpha):
+    """E[prod x_i^a_i] for x uniform on the unit sphere S^{d-1} (d = len(alpha)):
+    Gamma(d/2) / Gamma((n+d)/2) * prod Gamma((a_i+1)/2) / Gamma(1/2), zero if
+    any exponent is odd."""
+    d = len(alpha)
+    n = sum(alpha)
+    if any(a % 2 for a in alpha):
+        return 0.0
+    v = math.gamma(d / 2) / math.gamma((n + d) / 2)
+    for a in alpha:
+        v *= math.gamma((a + 1) / 2) / math.gamma(0.5)
+    return v
+
+
+def full_tensor(c, n, d):
+    """Expand independent components into the full symmetric d^n tensor (each
+    entry takes the value of the component of its sorted index multiset)."""
+    idx = O.multi_indices(n, d)
+    lookup = {tuple(a): k for k, a in enumerate(idx)}
+    T = np.zeros((d,) * n)
+    for ent in itertools.product(range(d), repeat=n):
+        cnt = tuple(ent.count(i) for i in range(d))
+        T[ent] = c[lookup[cnt]]
+    return T
+
+
+def contract(T, u, times):
+    for _ in range(times):
+        T = T @ u
+    return T
+
+
+def cube_matrices():
+    """The 24 proper rotations of the cube, as signed permutation matrices
+    with determinant +1 (built here independently of the oracle)."""
+    mats = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            P = np.zeros((3, 3))
+            for r, (c, s) in enumerate(zip(perm, signs)):
+                P[r, c] = s
+            if round(np.linalg.det(P)) == 1:
+                mats.append(P)
+    return mats
+
+
+def centred_grid(N):
+    c = N // 2
+    g = np.arange(N) - c
+    pz, py, px = np.meshgrid(g, g, g, indexing="ij")
+    return px, py, pz
+
+
+def permute_by(t, P):
+    """out(p) = t(P^T p) on an odd cubic grid (exact voxel permutation)."""
+    N = t.shape[0]
+    c = N // 2
+    px, py, pz = centred_grid(N)
+    Pv = np.stack([px.ravel(), py.ravel(), pz.ravel()])
+    src = (P.T @ Pv).round().astype(int) + c
+    return t[src[2], src[1], src[0]].reshape(t.shape)
+
+
+# ------------------------------------------------------------ index sets --
+
+def test_component_counts_match_paper():
+    # Sec. 3 after Alg. 2: n = 4 with quaternions (d' = 4) needs 35 correlations
+    assert O.num_components(4, 4) == int(golden("components_n4_d4"))
+    for n in (2, 4, 6):
+        assert O.num_components(n, 3) == (n + 1) * (n + 2) // 2
+    assert [O.num_components(n, 3) for n in (2, 4, 6)] == [6, 15, 28]
+
+
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4)])
+def test_multi_indices_enumerate_all_multisets(n, d):
+    a = O.multi_indices(n, d)
+    brute = {tuple(sum(1 for e in comb if e == i) for i in range(d))
+             for comb in itertools.combinations_with_replacement(range(d), n)}
+    assert set(map(tuple, a)) == brute
+    assert len(a) == len(brute)
+    # graded-lex descending: first exponents non-increasing lexicographically
+    assert [tuple(x) for x in a] == sorted(map(tuple, a), reverse=True)
+    # multiplicities count the full-tensor entries: they sum to d^n
+    m = O.multiplicities(n, d)
+    assert m.sum() == pytest.approx(d ** n)
+
+
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (4, 4)])
+def test_frobenius_of_tensor_power(n, d):
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=d)
+    a = O.multi_indices(n, d)
+    c = np.array([np.prod(v ** e) for e in a])  # components of v^{(x)n}
+    F = O.frobenius(c[:, None], n, d)[0]
+    assert F == pytest.approx(np.linalg.norm(v) ** n, rel=1e-12)
+    assert F == pytest.approx(np.linalg.norm(full_tensor(c, n, d)), rel=1e-12)
+
+
+# -------------------------------------------------------------- filter h --
+
+def test_filter_taps_and_response():
+    a = golden("filter_a")
+    assert 0 < a < golden("filter_a_upper")
+    f = np.zeros((5, 5, 5))
+    f[2, 2, 2] = 1.0
+    g = O.filter3(f, a)
+    taps = np.array([a, 1 - 2 * a, a])  # z-transform 1 + a(z + 1/z - 2)
+    assert np.allclose(g[1:4, 1:4, 1:4], np.einsum("i,j,k->ijk", taps, taps, taps), atol=1e-15)
+    assert g.sum() == pytest.approx(1.0)
+    # constant interior is preserved; zero padding loses one tap per touched edge
+    g1 = O.filter3(np.ones((6, 6, 6)), a)
+    assert np.allclose(g1[1:-1, 1:-1, 1:-1], 1.0)
+    assert g1[0, 0, 0] == pytest.approx((1 - a) ** 3)
+    # Nyquist along x: H(z = -1) = 1 - 4a
+    x = np.arange(8)
+    alt = np.broadcast_to((-1.0) ** x, (8, 8, 8)).copy()
+    ga = O.filter3(alt, a)
+    assert np.allclose(ga[1:-1, 1:-1, 1:-1], (1 - 4 * a) * alt[1:-1, 1:-1, 1:-1])
+
+
+# ------------------------------------------------------------------ mask --
+
+def test_mask_count_and_soft_edge():
+    m, M = O.mask((16, 16, 16), 7.0)
+    px, py, pz = centred_grid(16)
+    brute = int(np.sum(px ** 2 + py ** 2 + pz ** 2 <= 49))
+    assert M == brute == int(m.sum())
+    assert set(np.unique(m)) <= {0.0, 1.0}
+    ms, Ms = O.mask((21, 21, 21), 6.0, soft=2.0)
+    rho = np.sqrt(np.add.reduce([c.astype(float) ** 2 for c in centred_grid(21)]))
+    assert np.all(ms[rho <= 6] == 1.0)
+    assert np.all(ms[rho >= 8] == 0.0)
+    ramp = (rho > 6) & (rho < 8)
+    assert np.all((ms[ramp] > 0) & (ms[ramp] < 1))
+    order = np.argsort(rho[ramp])
+    assert np.all(np.diff(ms[ramp][order]) <= 1e-15)
+
+
+# ------------------------------------------------- template normalisation --
+
+def test_template_normalisation_eq4():
+    t = synth.gaussian_blob_template(15, seed=7)
+    m, M = O.mask(t.shape, 6.0)
+    tp, den = O.normalise_template(t, m)
+    assert np.all(tp[m == 0] == 0)
+    assert tp.sum() == pytest.approx(0.0, abs=1e-12)          # zero mean under the mask
+    assert (tp ** 2).sum() == pytest.approx(1.0, rel=1e-12)   # unit norm
+    # invariant to affine intensity changes (mask is 1+ voxel from the grid edge)
+    tp2, _ = O.normalise_template(3.5 * t - 2.0, m)
+    assert np.allclose(tp, tp2, atol=1e-12)
+
+
+# ------------------------------------------------------------- rotations --
+
+def test_superfib_constants_and_moments():
+    psi = O.superfib_psi()
+    assert psi ** 4 == pytest.approx(psi + 4, rel=1e-15)
+    q = O.superfib(4096)
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0)
+    # low-order moments of uniform S^3 points (the SO(3) Haar measure)
+    for alpha in [(2, 0, 0, 0), (0, 0, 2, 0), (1, 1, 0, 0), (4, 0, 0, 0), (2, 2, 0, 0),
+                  (0, 2, 0, 2)]:
+        est = np.mean(np.prod(q ** np.array(alpha), axis=1))
+        assert est == pytest.approx(sphere_moment(alpha), abs=2e-3)
+
+
+def test_quaternion_conventions():
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        R = O.quat_to_rot(q)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-14)
+        assert np.linalg.det(R) == pytest.approx(1.0)
+        # Rodrigues' formula for the same axis-angle
+        ang = 2 * math.acos(max(-1.0, min(1.0, q[0])))
+        ax = q[1:] / np.linalg.norm(q[1:])
+        Kx = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        Rr = np.eye(3) + math.sin(ang) * Kx + (1 - math.cos(ang)) * Kx @ Kx
+        assert np.allclose(R, Rr, atol=1e-12)
+    # rot(p q) = rot(p) rot(q)
+    p = np.array([0.5, 0.5, 0.5, 0.5])
+    q = np.array([math.cos(0.3), 0, math.sin(0.3), 0])
+    assert np.allclose(O.quat_to_rot(O.quat_mul(p, q)), O.quat_to_rot(p) @ O.quat_to_rot(q))
+
+
+def test_cube_group_is_the_cube_group():
+    qs = O.cube_rotations()
+    mats = [O.quat_to_rot(q) for q in qs]
+    ref = cube_matrices()
+    assert len(ref) == 24
+    for R in mats:
+        assert np.allclose(R, np.round(R), atol=1e-12)
+    key = lambda R: tuple(np.round(R).astype(int).ravel())
+    assert {key(R) for R in mats} == {key(P) for P in ref}
+
+
+def test_rotate_template_exact_for_cube_rotations():
+    t = synth.gaussian_blob_template(13, seed=11)
+    for q in O.cube_rotations():
+        R = O.quat_to_rot(q)
+        assert np.allclose(O.rotate_template(t, q), permute_by(t, np.round(R)), atol=1e-14)
+    # quarter-turn about z maps the +x axis onto +y: a blob at +x moves to +y
+    t = np.zeros((9, 9, 9))
+    t[4, 4, 7] = 1.0                       # (x,y,z) offset (3,0,0)
+    q90z = np.array([math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)])
+    r = O.rotate_template(t, q90z)
+    assert r[4, 7, 4] == pytest.approx(1.0)  # offset (0,3,0)
+
+
+# ---------------------------------------------------------- tensor field --
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_field_exact_under_cube_quadrature(n):
+    """Alg. 1 with Q = the 24 cube rotations and an odd template: every
+    resampling is an exact voxel permutation, so T_alpha(p) =
+    (1/24) sum_P (P e_z)^alpha t'(P^T p) can be written out exactly."""
+    t = synth.gaussian_blob_template(11, seed=5)
+    m, _ = O.mask(t.shape, 4.0)
+    tp, _ = O.normalise_template(t, m)
+    T = O.tensor_field(tp, O.cube_rotations(), n, 3)
+    alpha = O.multi_indices(n, 3)
+    ref = np.zeros_like(T)
+    for P in cube_matrices():
+        u = P[:, 2]
+        rot = permute_by(tp, P)
+        for k, a in enumerate(alpha):
+            ref[k] += np.prod(u ** a) * rot
+    ref /= 24.0
+    assert np.abs(T - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4)])
+def test_field_of_constant_is_sphere_moment(n, d):
+    """A constant t' is reproduced exactly by trilinear resampling away from
+    the grid edge, so T_alpha there equals the quadrature of E[u^alpha] over
+    S^2 (u = R e_z) or S^3 (u = q): a closed form."""
+    N = 9
+    tp = np.ones((N, N, N))
+    Q = O.rotation_set(256, cube=True)
+    T = O.tensor_field(tp, Q, n, d)
+    alpha = O.multi_indices(n, d)
+    ctr = T[:, N // 2, N // 2, N // 2]
+    ref = np.array([sphere_moment(tuple(a)) for a in alpha])
+    assert np.abs(ctr - ref).max() < 2e-3
+    # one voxel off-centre, still fully inside after any rotation
+    assert np.abs(T[:, N // 2 + 1, N // 2, N // 2 - 1] - ref).max() < 2e-3
+
+
+def test_field_quadrature_converges():
+    """Doubling the super-Fibonacci quadrature of Eq. 9 shrinks the change in T.
+    Trilinear resampling makes the integrand only continuous in R, so the
+    rate is slow: about 1e-3 relative at the default 24 x 2048 rotations."""
+    t = synth.gaussian_blob_template(16, seed=20240802)
+    m, _ = O.mask(t.shape, 7.0)
+    tp, _ = O.normalise_template(t, m)
+    T = {nb: O.tensor_field(tp, O.rotation_set(nb), 2, 3) for nb in (128, 256, 1024, 2048)}
+    scale = np.abs(T[2048]).max()
+    coarse = np.abs(T[256] - T[128]).max() / scale
+    fine = np.abs(T[2048] - T[1024]).max() / scale
+    assert fine < 0.25 * coarse
+    assert fine < 3e-3
+
+
+# ------------------------------------------------------ local normaliser --
+
+def test_local_w_linear_ramp_closed_form():
+    """g(x) = beta * x_x: S1 = beta M x, S2 = beta^2 (M x^2 + sum_ball p_x^2),
+    so var = beta^2 sum_{p in ball} p_x^2 exactly."""
+    Z = Y = X = 24
+    beta = 0.37
+    g = np.broadcast_to(beta * np.arange(X, dtype=float), (Z, Y, X)).copy()
+    m, M = O.mask((11, 11, 11), 4.0)
+    px, py, pz = centred_grid(11)
+    sum_px2 = float(np.sum(px[m > 0] ** 2))
+    vox = O.valid_voxels(g.shape, m.shape)[::97]
+    w, S1, S2 = O.local_w(g, m, vox)
+    xs = vox % X
+    assert np.allclose(S1, beta * M * xs, rtol=1e-12)
+    assert np.allclose(w, 1.0 / (beta * math.sqrt(sum_px2)), rtol=1e-10)
+    # constant image: zero variance -> w = 0 by the floor rule
+    wc, _, _ = O.local_w(np.full((Z, Y, X), 3.0), m, vox, floor=1e-12)
+    assert np.all(wc == 0)
+
+
+def test_local_w_periodic_agrees_in_interior():
+    g = synth.normals(9, 1, 20 ** 3).reshape(20, 20, 20)
+    m, _ = O.mask((7, 7, 7), 3.0)
+    vox = O.valid_voxels(g.shape, m.shape)
+    w0, _, _ = O.local_w(g, m, vox, periodic=False, floor=0.0)
+    w1, _, _ = O.local_w(g, m, vox, periodic=True, floor=0.0)
+    assert np.array_equal(w0, w1)
+
+
+# ----------------------------------------------------------- correlation --
+
+def test_correlation_of_delta_is_reflected_template():
+    """Eq. 5: (g * T)(x) = sum_p g(x+p) T(p); for g = delta at x0 this is
+    T(x0 - x) (correlation, not convolution)."""
+    Z = Y = X = 12
+    T = synth.gaussian_blob_template(5, seed=3)[None]
+    g = np.zeros((Z, Y, X))
+    x0 = (6, 5, 7)
+    g[x0] = 1.0
+    out = O.correlate(g, T, periodic=False)[0].reshape(Z, Y, X)
+    for x in [(6, 5, 7), (5, 5, 7), (6, 4, 8), (7, 6, 6), (4, 3, 5)]:
+        p = tuple(a - b for a, b in zip(x0, x))
+        expect = T[0][tuple(pi + 2 for pi in p)] if all(-2 <= pi <= 2 for pi in p) else 0.0
+        assert out[x] == pytest.approx(expect, abs=1e-15)
+
+
+def test_lncc_is_one_at_a_perfect_match():
+    """Eqs. 1-5: a tomogram holding an exact copy of the template (any
+    positive gain and offset) gives LNCC 1 at the copy's centre."""
+    N = 13
+    t = synth.gaussian_blob_template(N, seed=13)
+    m, M = O.mask(t.shape, 5.0)
+    tp, _ = O.normalise_template(t, m)
+    Z = Y = X = 32
+    f = np.zeros((Z, Y, X))
+    c0 = (15, 17, 14)
+    h = N // 2
+    f[c0[0] - h:c0[0] - h + N, c0[1] - h:c0[1] - h + N, c0[2] - h:c0[2] - h + N] = t
+    for gain, off in [(1.0, 0.0), (2.5, -0.7)]:
+        g = O.filter3(gain * f + off)
+        v = np.array([(c0[0] * Y + c0[1]) * X + c0[2]])
+        w, _, _ = O.local_w(g, m, v)
+        c = O.correlate(g, tp[None], v, w=w)[0, 0]
+        assert c == pytest.approx(1.0, abs=1e-12)
+
+
+def test_lncc_bounded_by_one_and_scale_invariant():
+    g = O.filter3(synth.normals(4, 1, 18 ** 3).reshape(18, 18, 18))
+    t = synth.gaussian_blob_template(7, seed=4)
+    m, _ = O.mask(t.shape, 3.0)
+    tp, _ = O.normalise_template(t, m)
+    vox = O.valid_voxels(g.shape, t.shape)
+    best, _ = O.tm(g, tp, O.cube_rotations(), vox, w=O.local_w(g, m, vox)[0])
+    assert np.all(np.abs(best) <= 1 + 1e-12)
+    best2, _ = O.tm(4.0 * g, tp, O.cube_rotations(), vox, w=O.local_w(4.0 * g, m, vox)[0])
+    assert np.allclose(best, best2, atol=1e-12)
+
+
+def test_tm_recovers_planted_quarter_turn():
+    """A copy rotated by a quarter-turn about z is found with LNCC 1 at that
+    rotation's index -- and not at the inverse quarter-turn."""
+    N = 11
+    t = synth.gaussian_blob_template(N, seed=21)
+    m, _ = O.mask(t.shape, 4.0)
+    tp, _ = O.normalise_template(t, m)
+    s = math.sqrt(0.5)
+    quats = np.array([[1, 0, 0, 0], [s, 0, 0, s], [s, 0, 0, -s], [0, 0, 0, 1.0]])
+    R = O.quat_to_rot(quats[1])
+    Z = Y = X = 27
+    f = np.zeros((Z, Y, X))
+    c0 = (13, 13, 13)
+    h = N // 2
+    f[c0[0] - h:c0[0] + h + 1, c0[1] - h:c0[1] + h + 1, c0[2] - h:c0[2] + h + 1] = permute_by(t, np.round(R))
+    g = O.filter3(f)
+    v = np.array([(c0[0] * Y + c0[1]) * X + c0[2]])
+    w, _, _ = O.local_w(g, m, v)
+    best, idx = O.tm(g, tp, quats, v, w=w)
+    assert idx[0] == 1
+    assert best[0] == pytest.approx(1.0, abs=1e-12)
+
+
+# ------------------------------------------------------------- maximiser --
+
+def test_maximiser_order2_is_top_eigenpair():
+    C = synth.random_tensors(17, 40, 6).T.copy()   # [K][nvox]
+    s, u, _ = O.maximise(C, 2, 3, nsamples=2000)
+    for i in range(C.shape[1]):
+        c = C[:, i]
+        A = np.array([[c[0], c[1], c[2]], [c[1], c[3], c[4]], [c[2], c[4], c[5]]])
+        ev, V = np.linalg.eigh(A)
+        assert s[i] == pytest.approx(ev[-1], abs=1e-12)
+        assert abs(abs(u[i] @ V[:, -1]) - 1) < 1e-10
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_maximiser_rank_one_and_two(n):
+    rng = np.random.default_rng(n)
+    a = O.multi_indices(n, 3)
+    for _ in range(5):
+        Qm, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        v1, v2 = Qm[:, 0], Qm[:, 1]
+        l1, l2 = 2.0, 1.3
+        c = np.array([l1 * np.prod(v1 ** e) + l2 * np.prod(v2 ** e) for e in a])
+        s, u, _ = O.maximise(c[:, None], n, 3, nsamples=4000)
+        assert s[0] == pytest.approx(l1, abs=1e-12)
+        assert abs(abs(u[0] @ v1) - 1) < 1e-10
+        assert u[0][2] >= 0  # canonical half-sphere
+
+
+@pytest.mark.parametrize("n,d", [(4, 3), (6, 3), (4, 4)])
+def test_maximiser_random_tensors_against_full_tensor(n, d):
+    K = O.num_components(n, d)
+    C = synth.random_tensors(100 + n + d, 12, K).T.copy()
+    s, u, _ = O.maximise(C, n, d, nsamples=20000)
+    F = O.frobenius(C, n, d)
+    rng = np.random.default_rng(5)
+    dirs = rng.normal(size=(100000, d))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    for i in range(C.shape[1]):
+        T = full_tensor(C[:, i], n, d)
+        ui = u[i]
+        # the oracle's polynomial is the tensor's form: p(u) = T . u^n
+        assert O.poly_eval(C[:, i], n, d, ui)[0] == pytest.approx(contract(T, ui, n), abs=1e-12)
+        # Z-eigenpair: T u^{n-1} = s u
+        assert np.linalg.norm(contract(T, ui, n - 1) - s[i] * ui) < 1e-10
+        # Riemannian Hessian negative semidefinite at the maximum
+        H = n * (n - 1) * contract(T, ui, n - 2)
+        Pm = np.eye(d) - np.outer(ui, ui)
+        Hr = Pm @ H @ Pm - n * s[i] * Pm
+        assert np.linalg.eigvalsh(Hr).max() < 1e-8
+        # s <= ||T||_F, and no random direction beats it
+        assert s[i] <= F[i] + 1e-12
+        brute = batch_form(T, dirs, n)
+        assert brute.max() <= s[i] + 1e-12
+        assert s[i] - brute.max() < 5e-3 * F[i]
+        # the sphere mean bounds the max from below
+        assert s[i] >= brute.mean() - 1e-12
+
+
+def batch_form(T, U, n):
+    """T . u^n for every row u of U (contract all n axes)."""
+    vals = np.empty(U.shape[0])
+    for j in range(0, U.shape[0], 5000):
+        blk = U[j:j + 5000]
+        R = np.tensordot(blk, T, axes=([1], [0]))        # (b, d, ..., d)
+        for _ in range(n - 1):
+            R = np.einsum("bi,bi...->b...", blk, R)
+        vals[j:j + 5000] = R
+    return vals
+
+
+
+def test_spectral_bound_reported():
+    """Sec. 3.2 quotes ||T||_sigma >= ||T||_F / 2^{n-1}; log the worst ratio
+    seen on random tensors (informational, not a gate)."""
+    n = 4
+    C = synth.random_tensors(77, 50, 15).T.copy()
+    s, _, _ = O.maximise(C, n, 3, nsamples=4000)
+    F = O.frobenius(C, n, 3)
+    # spectral norm = max |p| = max(max p, -min p); max p alone already bounds it below
+    ratio = (np.abs(s) / F).min()
+    assert ratio > 0
+
+
+# ---------------------------------------------------------------- peaks --
+
+def test_find_peaks_order_exclusion_and_ties():
+    s = np.zeros((10, 10, 10))
+    s[2, 2, 2] = 5.0
+    s[2, 2, 5] = 4.0      # 3 voxels from the first: excluded at min_dist 4
+    s[7, 7, 7] = 3.0
+    s[7, 7, 3] = 3.0      # tie with (7,7,7): lower linear index first
+    s[2, 8, 8] = 1.0      # >= 4 from every accepted peak
+    box = (0, 10, 0, 10, 0, 10)
+    idx, val = O.find_peaks(s, box, 10, 4.0)
+    lin = lambda z, y, x: (z * 10 + y) * 10 + x
+    assert list(idx) == [lin(2, 2, 2), lin(7, 7, 3), lin(7, 7, 7), lin(2, 8, 8)]
+    assert list(val) == [5.0, 3.0, 3.0, 1.0]
+    idx2, _ = O.find_peaks(s, box, 2, 4.0)
+    assert list(idx2) == [lin(2, 2, 2), lin(7, 7, 3)]
+    # each plateau yields one peak, at its lowest linear index (the zero
+    # background is a plateau too)
+    p = np.zeros((6, 6, 6))
+    p[2:4, 2:4, 2:4] = 1.0
+    idx3, _ = O.find_peaks(p, (0, 6, 0, 6, 0, 6), 5, 1.0)
+    assert list(idx3) == [lin6(2, 2, 2), 0]
+
+
+def lin6(z, y, x):
+    return (z * 6 + y) * 6 + x
+
+
+# ------------------------------------------------------ end-to-end pins --
+
+@pytest.mark.slow
+def test_ttm_invariant_under_quarter_turns_of_the_tomogram():
+    """With a cube-symmetrised quadrature and an odd template, rotating a
+    cubic tomogram by a quarter-turn rotates the score map with it and the
+    orientation by the same rotation (exact up to rounding)."""
+    L, N = 21, 7
+    tomo = synth.normals(31, 1, L ** 3).reshape(L, L, L)
+    tmpl = synth.gaussian_blob_template(N, seed=31)
+    Q = O.rotation_set(64, cube=True)
+    vox = O.valid_voxels((L, L, L), (N, N, N))
+    base = O.ttm(tomo, tmpl, 3.0, 4, Q, vox, nsamples=3000)
+    # quarter-turn about z (x -> y): array axes (z, y, x), rotate in the (y, x) plane
+    P = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1.0]])   # acting on (x, y, z)
+    rot = permute_by(tomo, P)
+    moved = O.ttm(rot, tmpl, 3.0, 4, Q, vox, nsamples=3000)
+    s0 = base["score"].reshape(-1)
+    # voxel x (offset p from the volume centre) maps to P p
+    c = L // 2
+    zz, yy, xx = np.unravel_index(vox, (L, L, L))
+    pv = np.stack([xx - c, yy - c, zz - c])
+    q = (P @ pv).round().astype(int) + c
+    vmap = (q[2] * L + q[1]) * L + q[0]
+    pos = {v: i for i, v in enumerate(vox)}
+    j = np.array([pos[v] for v in vmap])
+    assert np.abs(moved["score"][j] - s0).max() < 1e-10
+    ok = (base["score"] - base["second"]) > 1e-3 * np.abs(base["score"])
+    u0 = base["orient"] @ P.T
+    dots = np.abs(np.sum(u0[ok] * moved["orient"][j][ok], axis=1))
+    assert np.all(dots > 1 - 1e-9)
