@@ -1,0 +1,307 @@
+"""Benchmark of the tensorial template matching hot path on GB300.
+
+One step = the whole per-tomogram path on one tomogram: tensorial
+correlation with local normalisation (ttm_correlate: prefilter, image
+spectrum, FP64 local sums, fused z pass, y pass, x pass with the w
+epilogue) and the score + orientation maps (ttm_peak_map). The tensor field
+(built once per template) is outside the timed region, as in the paper.
+
+Workload: 512 x 512 x 200 float32 tomogram of Gaussian-low-passed noise
+(sigma = 1) with 300 copies of a 40^3 six-Gaussian template planted at
+uniform random rotations (SNR 0.1), tensor order 4 (15 components), mask
+radius 16. Inputs (210 MB tomogram, 3.1 GB C maps) are larger than L2, so no
+explicit flush between steps.
+
+Prints one JSON line. `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ttm_n4_512x512x200_t40_r16_300copies_snr0.1"
+METRIC = "TTM voxels/s (score+orientation map)"
+UNIT = "voxels/s"
+
+
+def peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("TTM_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_sample_rate(wl, n_voxels: int, seed: int = 1):
+    """Time the FP64 oracle on n_voxels of the valid interior: local
+    normaliser, direct-sum tensorial correlation and dense-sampling +
+    Newton maximiser. Setup (filter of the volume, template normalisation
+    and a field built with 192 rotations -- the per-voxel cost of the timed
+    steps does not depend on the quadrature size) is excluded."""
+    import oracle as O
+    n = wl.order_n
+    pr = O.Prepared(wl.tomo, wl.template, wl.mask_radius)
+    T = O.tensor_field(pr.tp, O.rotation_set(8), n, 3)
+    vox = O.valid_voxels(pr.g.shape, pr.tshape)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(vox.size, size=min(n_voxels, vox.size), replace=False))
+    v = vox[sel]
+    t0 = time.perf_counter()
+    w, _, _ = O.local_w(pr.g, pr.m, v, False, pr.floor)
+    C = O.correlate(pr.g, T, v, False, w)
+    O.maximise(C, n, 3, 20000)
+    dt = time.perf_counter() - t0
+    return v.size / dt, v.size, dt, O.num_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2408_02398_gb300 import synth
+    wl = synth.workload_order4()
+    # calibrate the sample so the whole run stays within a few minutes
+    rate0, _, _, cores = oracle_sample_rate(wl, 200)
+    per_step = max(200, int(rate0 * 8.0))
+    times = []
+    nv = 0
+    for i in range(args.warmup + args.steps):
+        r, nv, dt, cores = oracle_sample_rate(wl, per_step, seed=i + 2)
+        if i >= args.warmup:
+            times.append(dt)
+    value = nv * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_voxels_per_step": nv},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d random valid-interior voxels per step: local normaliser, direct-sum "
+                                       "correlation (15 components), 20000-sample + Newton maximiser" % nv},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU path --
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2408_02398_gb300 import build, synth
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.workload_order4()
+    Z, Y, X = wl.tomo.shape
+    V = Z * Y * X
+    n = wl.order_n
+    K = ttm.ttm_num_components(n)
+    ctx = ttm.Context(local)
+    p = ttm.params(order_n=n, mask_radius=wl.mask_radius, n_rot_base=2048)
+    t0 = time.perf_counter()
+    m = ttm.Matcher(ctx, wl.template, p, (Z, Y, X), device=dev)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ttm.ttm_correlate(m.plan, d_tomo, m.C)
+        ttm.ttm_peak_map(m.plan, m.C, m.score, m.orient, m.frob)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ttm.ttm_plan_stage_times(m.plan)  # discard
+    ttm.ttm_plan_enable_timing(m.plan, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ttm.ttm_kernel_launches()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = ttm.ttm_kernel_launches() - launches0
+    ms_total = e0.elapsed_time(e1)
+    stages = ttm.ttm_plan_stage_times(m.plan)
+    ttm.ttm_plan_enable_timing(m.plan, False)
+    ck = clocks.stop()
+    ms_total = max_over_ranks(ms_total, ws, dev)
+    ms_step = ms_total / args.steps
+    value = V * args.steps * ws / (ms_total / 1e3)
+
+    # end to end through the public API with host buffers: pinned tomogram
+    # in, score + orientation maps out, copies inside the timed region
+    h_tomo = torch.from_numpy(wl.tomo).pin_memory()
+    h_score = torch.empty((Z, Y, X), dtype=torch.float32).pin_memory()
+    h_orient = torch.empty((3, Z, Y, X), dtype=torch.float32).pin_memory()
+    d_in = torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+
+    def e2e_step():
+        d_in.copy_(h_tomo, non_blocking=True)
+        ttm.ttm_correlate(m.plan, d_in, m.C)
+        ttm.ttm_peak_map(m.plan, m.C, m.score, m.orient, m.frob)
+        h_score.copy_(m.score, non_blocking=True)
+        h_orient.copy_(m.orient, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws, dev)
+    e2e_value = V * args.steps * ws / (ms_e2e / 1e3)
+
+    # roofline of the dominant part. Stages are per-step milliseconds.
+    st_ms = {k: v / args.steps for k, v in stages.items()}
+    corr_ms = sum(v for k, v in st_ms.items() if k != "peak_map")
+    pk, how = peaks_file()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    alg_bytes_corr = (4 + 4 * K) * V          # read f, write K normalised maps
+    roof = {"bound": "hbm", "kernel": "ttm_correlate (fused correlate path, stages 0-5)",
+            "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_source": how, "traffic": None, "bytes_per_voxel": 4 + 4 * K}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, nv, dt, cores = oracle_sample_rate(wl, args.cpu_voxels)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d random valid-interior voxels (%.1f s): local normaliser, direct-sum correlation "
+                         "(15 components), 20000-sample + Newton maximiser; setup excluded" % (nv, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "shape_zyx": [Z, Y, X], "template": 40, "order_n": n,
+                           "components": K, "mask_radius": wl.mask_radius, "rotations_field": 24 * 2048,
+                           "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1gpu",
+                           "local_sums": "fp64", "spectra": "fp32"},
+                "roofline": roof, "stages_ms": st_ms, "setup_s": setup_s,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": V * 4,
+                        "d2h_bytes_per_step": V * 4 * 4},
+                "gpu_launches": int(launches), "clocks": ck}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-voxels", type=int, default=60000)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * ttm.h -- C ABI of libttm: tensorial template matching (TTM) on one GB300
+ * GPU (sm_103a), after Martinez-Sanchez, Homberg, Almira & Phelippeau,
+ * "Tensorial template matching for fast cross-correlation with rotations and
+ * its application for tomography" (ECCV 2024).
+ *
+ * Conventions (all entry points):
+ *   - Volumes are C-order float32 arrays [Z][Y][X], x fastest. A template of
+ *     extent (tz,ty,tx) has its centre at (tz/2, ty/2, tx/2); offsets are
+ *     p = (ix-cx, iy-cy, iz-cz) and vectors are ordered (x, y, z).
+ *   - A symmetric tensor of degree n over R^3 is stored by its K =
+ *     binom(n+2, 2) independent components (the full-tensor entries), in
+ *     graded-lex descending order of the exponents (a,b,c) of (x,y,z): for
+ *     n = 2 that is xx, xy, xz, yy, yz, zz. Multi-component fields are
+ *     structure-of-arrays [K][...].
+ *   - Quaternions are (w, x, y, z); rotation R(q) acts on column vectors and
+ *     a rotated template is t_R(p) = t(R^T p) (trilinear, zero outside).
+ *   - Pointers named d_* are device pointers, h_* host pointers. All buffers
+ *     are owned by the caller; the library allocates only in *_create calls
+ *     (context workspace, plans) and never inside the compute calls.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls
+ *     are asynchronous on it unless stated otherwise.
+ *   - Every call returns a ttm_status; TTM_OK is 0. On failure nothing has
+ *     been written to the outputs except where stated, and a message is kept
+ *     in the context (ttm_last_error). No C++ exception crosses this ABI.
+ *   - Results are defined on the valid interior: voxels whose whole template
+ *     window lies inside the volume. Outside it values are finite but
+ *     implementation defined (the correlation wraps around the grid there).
+ */
+#ifndef TTM_H
+#define TTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TTM_OK = 0,
+    TTM_E_INVALID_ARG = 1, /* null pointer, bad enum, bad parameter */
+    TTM_E_SHAPE = 2,       /* volume smaller than the template, or size not supported */
+    TTM_E_UNSUPPORTED = 3, /* order n / d' / precision not built */
+    TTM_E_OOM = 4,         /* device allocation failed in a *_create call */
+    TTM_E_CUDA = 5,        /* a CUDA runtime call failed (message in ttm_last_error) */
+    TTM_E_TIMEOUT = 6,     /* a bounded device wait expired */
+    TTM_E_INTERNAL = 7
+} ttm_status;
+
+typedef enum {
+    TTM_PREC_FP32 = 0,         /* template spectra stored and multiplied in FP32 */
+    TTM_PREC_FP16_SPECTRA = 1, /* spectra in FP16 with a per-component scale, FP32 accumulate */
+    TTM_PREC_BF16_SPECTRA = 2  /* spectra in BF16 with a per-component scale, FP32 accumulate */
+} ttm_precision;
+
+typedef enum {
+    TTM_MAX_PLAIN = 0,   /* probe directions + Newton polish */
+    TTM_MAX_MLP_WARM = 1 /* learned warm start, plain maximiser as fallback */
+} ttm_maximiser;
+
+typedef struct ttm_ctx ttm_ctx;
+typedef struct ttm_plan ttm_plan;
+
+/* Parameters of the tensor field and of the local normalisation.
+ *   order_n          tensor degree n (even; 2, 4 or 6 are built)
+ *   dprime           3: the weight of rotation R is (R e_z)^{(x)n}, maximised
+ *                    over unit directions u in S^2 (K = binom(n+2,2));
+ *                    4: quaternion powers q^{(x)n} as in Sec. 3 (oracle only
+ *                    in this version: TTM_E_UNSUPPORTED on the GPU)
+ *   mask_radius      r of the spherical mask m (Sec. 2, after Eq. 3), voxels
+ *   mask_soft_width  width of the raised-cosine edge beyond r; 0 = binary
+ *   filter_a         a of the filter h with z-transform 1 + a(z + 1/z - 2)
+ *                    (Sec. 2; the paper uses 1/5); 0 disables the filter
+ *   n_rot_base       super-Fibonacci samples of SO(3) for Eq. 9
+ *   cube_symmetrize  1: the quadrature is the 24 cube rotations times the
+ *                    base samples (24 * n_rot_base rotations)            */
+typedef struct {
+    int order_n;
+    int dprime;
+    double mask_radius;
+    double mask_soft_width;
+    double filter_a;
+    int64_t n_rot_base;
+    int cube_symmetrize;
+} ttm_field_params;
+
+/* Fills p with the defaults: n = 4, d' = 3, r = 16, soft 0, a = 0.2,
+ * 2048 base rotations, cube symmetrisation on. */
+void ttm_default_params(ttm_field_params* p);
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device` (makes it current). */
+ttm_status ttm_ctx_create(int device, ttm_ctx** out);
+void ttm_ctx_destroy(ttm_ctx* ctx);
+/* Text of the last failure on this context ("" if none). Owned by ctx. */
+const char* ttm_last_error(const ttm_ctx* ctx);
+/* binom(n + d' - 1, n): the number of independent components (Sec. 3). */
+int ttm_num_components(int order_n, int dprime);
+/* Library version string, e.g. "ttm 0.1 sm_103a". */
+const char* ttm_version(void);
+
+/* The rotation quadrature of Eq. 9 (host only, no device work): n_base
+ * super-Fibonacci unit quaternions (Alexa, CVPR 2022; the sampling the paper
+ * uses in Sec. 3 and Sec. 3.4), optionally left-multiplied by the 24 cube
+ * rotations (entry i*24 + j = c_j * q_i). h_quats receives 4 * count
+ * doubles where count = n_base * (cube ? 24 : 1). */
+ttm_status ttm_rotation_set(int64_t n_base, int cube, double* h_quats);
+
+/* ----------------------------------------------------- step a0: Alg. 1 */
+
+/* Tensor template (Eq. 9, Alg. 1): normalises the template (Eq. 4: filter
+ * h, mask m, zero mean and unit norm under the mask) into t', then
+ * T_alpha(p) = (1/|Q|) sum_q u_q^alpha t'(R_q^T p) over the quadrature of
+ * `params` (u_q = R_q e_z), all in FP64 on the GPU.
+ *   d_tmpl   float32 [tz][ty][tx] raw template (device)
+ *   d_field  float64 [K][tz][ty][tx] output (device), K = ttm_num_components
+ * Blocking: returns once the field has been written. */
+ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, int tz, int ty, int tx,
+                                  const ttm_field_params* params, double* d_field, void* stream);
+
+/* -------------------------------------------------- steps a1-a2: Alg. 2 */
+
+/* A plan binds a tensor field to one tomogram shape: it holds the template
+ * spectra (transformed along x and y, kept on the template's z rows), the
+ * spectrum of the mask, and the per-tomogram workspace. Allocates device
+ * memory (~ (K + 6) * Z*Y*(X/2+1) * 8 bytes for FP32). Blocking. */
+ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                           const ttm_field_params* params, int Z, int Y, int X,
+                           ttm_precision precision, ttm_plan** out);
+void ttm_plan_destroy(ttm_plan* plan);
+/* Number of components K of the plan. */
+int ttm_plan_components(const ttm_plan* plan);
+/* Valid-interior box of the plan: z0,z1,y0,y1,x0,x1 (half-open). */
+void ttm_plan_valid_box(const ttm_plan* plan, int* box6);
+
+/* Tensorial correlation C_alpha(x) = w(x) (g * T_alpha)(x) (Eq. 8, Alg. 2)
+ * with g = h * f (Eq. 3, zero padded), the correlation of Eq. 5 evaluated
+ * through FFTs (periodic on the Z x Y x X grid), and the local normaliser
+ * of Eq. 2: w = 1/sqrt(S2 - S1^2/M), S1 = sum m g(x+.), S2 = sum m^2
+ * g(x+.)^2, computed in FP64; w = 0 where the local variance is at most
+ * 1e-12 * M * var(g).
+ *   d_tomo  float32 [Z][Y][X] (device)
+ *   d_C     float32 [K][Z][Y][X] output (device) */
+ttm_status ttm_correlate(ttm_plan* plan, const float* d_tomo, float* d_C, void* stream);
+
+/* Local normaliser w of the last ttm_correlate on this plan, float32
+ * [Z][Y][X] copied to d_w (device). */
+ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream);
+
+/* ---------------------------------------------------- steps a3-a4: Sec. 3.1-3.2 */
+
+/* Per voxel: score s(x) = max over unit u of C(x) . u^{(x)n} (the dominant
+ * Z-eigenvalue, Sec. 3.1), orientation u*(x) (the maximiser, on the
+ * half-sphere whose last non-zero coordinate is positive) and the Frobenius
+ * proxy ||C(x)||_F (Sec. 3.2).
+ *   d_C       float32 [K][Z][Y][X] (device, from ttm_correlate)
+ *   d_score   float32 [Z][Y][X]; d_orient float32 [3][Z][Y][X] (u_x, u_y, u_z)
+ *   d_frob    float32 [Z][Y][X] or NULL
+ *   mlp       must be NULL for TTM_MAX_PLAIN */
+ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, const void* mlp,
+                        float* d_score, float* d_orient, float* d_frob, void* stream);
+
+/* --------------------------------------------------------- step a5: Sec. 3.4 */
+
+/* Find Peaks: the P highest local maxima (26-neighbourhood, within the valid
+ * box; ties broken by lower linear index) of d_map [Z][Y][X] that keep a
+ * Euclidean distance >= min_dist (the paper: 2 x mask radius) to every
+ * higher accepted peak. Writes up to P linear indices and values to host
+ * arrays and the count to *h_count. Synchronises `stream`. */
+ttm_status ttm_find_peaks(ttm_plan* plan, const float* d_map, int P, double min_dist,
+                          int64_t* h_idx, float* h_val, int* h_count, void* stream);
+
+/* ------------------------------------------------------- step a6: Eqs. 1, 6, 7 */
+
+/* Classical template matching baseline: for every rotation q_j of h_quats
+ * (4 * n_rot doubles, any order), c(x, R_j) = w(x) (g * t'_{R_j})(x) with
+ * t' of Eq. 4; d_best[x] = max_j c, d_best_idx[x] = the first j attaining
+ * it. Uses the same filter, mask and normaliser as ttm_correlate.
+ *   d_tomo float32 [Z][Y][X]; d_tmpl float32 [tz][ty][tx] raw template
+ *   d_best float32 [Z][Y][X]; d_best_idx int32 [Z][Y][X] (device)
+ * Allocates its workspace for the duration of the call (blocking). */
+ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int Y, int X, const float* d_tmpl,
+                        int tz, int ty, int tx, const ttm_field_params* params,
+                        const double* h_quats, int64_t n_rot, float* d_best, int32_t* d_best_idx,
+                        void* stream);
+
+/* ------------------------------------------------------------ tracing */
+
+/* Per-stage timing of a plan with CUDA events recorded on the stream of
+ * each call (off by default). Stages: 0 prefilter + variance floor,
+ * 1 image spectrum, 2 FP64 local sums -> w, 3 fused z pass, 4 y pass,
+ * 5 x pass with the w epilogue, 6 peak map. ttm_plan_stage_times
+ * synchronises, adds the elapsed milliseconds of every call since the last
+ * reset into ms[0..n-1] (n <= ttm_num_stages()) and clears the record. */
+ttm_status ttm_plan_enable_timing(ttm_plan* plan, int on);
+ttm_status ttm_plan_stage_times(ttm_plan* plan, double* ms, int n);
+int ttm_num_stages(void);
+const char* ttm_stage_name(int i);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t ttm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTM_H */

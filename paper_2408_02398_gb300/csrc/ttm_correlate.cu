@@ -1,0 +1,262 @@
+// ttm_correlate.cu -- Alg. 2 (tensorial field) on the GPU:
+//   C_alpha = w * IFFT( FFT(g) * conj(FFT(T_alpha)) )       (Eqs. 5, 8)
+//
+// The template spectra are kept "partial": transformed along x and y only,
+// on the template's own z rows (tz of the Z rows), so the plan holds
+// K * tz * Y * (X/2+1) values instead of K * Z * Y * (X/2+1). The inverse
+// transform of every component starts with a fused z pass: one CTA loads a
+// tile of image-spectrum columns once, and for each component places the
+// tz template rows on their wrapped z positions, finishes the template
+// transform along z, multiplies by the image spectrum (conjugated template)
+// and transforms back along z. Then a y pass over all K components and an
+// x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
+#include <vector>
+
+#include "ttm_internal.h"
+
+namespace ttm {
+
+// component alpha of the FP64 field, placed at the origin of a tz x Y x X
+// grid (wrapped in y and x; z rows are the template's rows j = 0..tz-1)
+struct SrcFieldRows {
+    const double* T;
+    int Y, X, ty, tx;
+    __device__ double operator()(int64_t row, int x) const
+    {
+        int j = (int)(row / Y), y = (int)(row - (int64_t)j * Y);
+        int iy = wrap_to_template(y, Y, ty), ix = wrap_to_template(x, X, tx);
+        if (iy < 0 || ix < 0) return 0.0;
+        return T[((int64_t)j * ty + iy) * tx + ix];
+    }
+};
+
+__global__ void k_spec_store(const double2* __restrict__ src, int64_t n, double scale, float2* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = src[i];
+        dst[i] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+    }
+}
+
+// Fused z pass. Columns c in [0, ncols) (ncols = Y * Xh) are the (ky, kx)
+// pairs; element z of column c is at z * ncols + c. One CTA owns W adjacent
+// columns. Shared memory: 3 * W * ld + Z complex.
+__global__ void __launch_bounds__(256)
+k_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
+        float2* __restrict__ out, LenPlan pl, int W, int ld)
+{
+    extern __shared__ unsigned char smem_raw[];
+    float2* gs = reinterpret_cast<float2*>(smem_raw);
+    float2* bufa = gs + W * ld;
+    float2* bufb = bufa + W * ld;
+    float2* tws = bufb + W * ld;
+    const int Z = pl.L;
+    const int64_t c0 = (int64_t)blockIdx.x * W;
+    load_twiddles<float>(tws, pl);
+    for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+        int z = idx / W, w = idx - z * W;
+        int64_t c = c0 + w;
+        gs[w * ld + z] = c < ncols ? G[(int64_t)z * ncols + c] : make_float2(0.f, 0.f);
+    }
+    const int64_t comp_stride = (int64_t)tzn * ncols;
+    const int64_t out_stride = (int64_t)Z * ncols;
+    for (int a = 0; a < K; a++) {
+        // template rows j land on z = (j - cz) mod Z, i.e. j = (z + cz) mod Z
+        const float2* sp = spec + a * comp_stride;
+        for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+            int z = idx / W, w = idx - z * W;
+            int64_t c = c0 + w;
+            int j = z + cz;
+            if (j >= Z) j -= Z;
+            float2 v = make_float2(0.f, 0.f);
+            if (j < tzn && c < ncols) v = sp[(int64_t)j * ncols + c];
+            bufa[w * ld + z] = v;
+        }
+        __syncthreads();
+        float2* p = smem_fft<-1, float>(bufa, bufb, ld, W, pl, tws);
+        float2* q = (p == bufa) ? bufb : bufa;
+        for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+            int w = idx / Z, z = idx - w * Z;
+            p[w * ld + z] = cmulconj(gs[w * ld + z], p[w * ld + z]);
+        }
+        __syncthreads();
+        float2* r = smem_fft<+1, float>(p, q, ld, W, pl, tws);
+        float2* o = out + a * out_stride;
+        for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+            int z = idx / W, w = idx - z * W;
+            int64_t c = c0 + w;
+            if (c < ncols) o[(int64_t)z * ncols + c] = r[w * ld + z];
+        }
+        __syncthreads();
+    }
+}
+
+// epilogue of the x pass: C_alpha(x) = w(x) * value
+struct SinkNormalise {
+    float* C;
+    const float* w;
+    int64_t V;
+    int X;
+    __device__ void operator()(int batch, int64_t row, int x, float v) const
+    {
+        int64_t i = row * X + x;
+        C[(int64_t)batch * V + i] = w[i] * v;
+    }
+};
+
+void launch_zcorr(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
+                  const LenPlan& pz, cudaStream_t st)
+{
+    const int Z = pz.L;
+    const int ld = (Z % 2 == 0) ? Z + 1 : Z;
+    int W = 16;
+    while (W > 2 && (3 * (size_t)W * ld + Z) * sizeof(float2) > 112 * 1024) W /= 2;
+    size_t smem = (3 * (size_t)W * ld + Z) * sizeof(float2);
+    set_smem(k_zcorr, smem);
+    int64_t grid = ceil_div(ncols, W);
+    k_zcorr<<<(unsigned)grid, 256, smem, st>>>(G, spec, K, tzn, cz, ncols, out, pz, W, ld);
+    TTM_LAUNCH_CHECK();
+}
+
+void plan_build_spectra(ttm_plan* P, const double* d_field)
+{
+    Prep& p = P->prep;
+    const int Y = p.Y, X = p.X, Xh = p.Xh, tz = p.tz, ty = p.ty, tx = p.tx;
+    const int64_t V = (int64_t)p.Z * Y * X;
+    const int64_t ncomp = (int64_t)tz * Y * Xh;
+    P->spec.alloc(P->K * ncomp * sizeof(float2));
+    double2* scratch = p.zc.as<double2>();  // tz*Y*Xh <= Z*Y*X
+    cudaStream_t st = 0;
+    for (int a = 0; a < P->K; a++) {
+        const double* Ta = d_field + (int64_t)a * tz * ty * tx;
+        launch_r2c_rows<double>(SrcFieldRows{Ta, Y, X, ty, tx}, (int64_t)tz * Y, scratch, p.px64, st);
+        launch_strided<double, -1>(scratch, StridedAxis{Xh, tz, (int64_t)Y * Xh, Xh}, p.py64,
+                                   ProIdentity<double>(), StoreTo<double>{scratch, (int64_t)Y * Xh, Xh}, st);
+        k_spec_store<<<1024, 256, 0, st>>>(scratch, ncomp, 1.0 / (double)V, P->spec.as<float2>() + a * ncomp);
+        TTM_LAUNCH_CHECK();
+    }
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st)
+{
+    Prep& p = P->prep;
+    const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
+    const int64_t ncols = (int64_t)Y * Xh;
+    const int64_t V = (int64_t)Z * Y * X;
+    stage_begin(P, st);
+    prep_filter(p, d_tomo, st);
+    stage_end(P, ST_FILTER, st);
+    prep_spectrum(p, st);
+    stage_end(P, ST_SPECTRUM, st);
+    prep_localsums(p, st);
+    stage_end(P, ST_LOCALSUM, st);
+    float2* work = P->work.as<float2>();
+    launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32, st);
+    stage_end(P, ST_ZCORR, st);
+    launch_strided<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
+                              StoreTo<float>{work, ncols, Xh}, st);
+    stage_end(P, ST_YPASS, st);
+    launch_c2r_rows<float>(work, (int64_t)Z * Y, SinkNormalise{d_C, p.w.as<float>(), V, X}, p.px32, P->K, st);
+    stage_end(P, ST_XPASS, st);
+}
+
+}  // namespace ttm
+
+using namespace ttm;
+
+static bool params_ok(const ttm_field_params* fp, std::string& why)
+{
+    if (!fp) { why = "params is NULL"; return false; }
+    if (fp->order_n < 2 || fp->order_n > 6 || fp->order_n % 2) { why = "order_n must be 2, 4 or 6"; return false; }
+    if (fp->dprime != 3 && fp->dprime != 4) { why = "dprime must be 3 or 4"; return false; }
+    if (!(fp->mask_radius > 0)) { why = "mask_radius must be positive"; return false; }
+    if (!(fp->mask_soft_width >= 0)) { why = "mask_soft_width must be >= 0"; return false; }
+    if (!(fp->filter_a >= 0 && fp->filter_a < 0.25)) { why = "filter_a must be in [0, 0.25)"; return false; }
+    return true;
+}
+
+// the mask must be symmetric on the template grid: for an even extent the
+// face at offset -t/2 has no mirror, so it must lie outside the mask
+static bool mask_fits(int t, const ttm_field_params* fp)
+{
+    return (t % 2) ? (fp->mask_radius + fp->mask_soft_width <= (t - 1) / 2.0 + 1e-9)
+                   : (fp->mask_radius + fp->mask_soft_width < t / 2.0);
+}
+
+extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                                      const ttm_field_params* params, int Z, int Y, int X,
+                                      ttm_precision precision, ttm_plan** out)
+{
+    if (!ctx) return TTM_E_INVALID_ARG;
+    ttm_plan* P = nullptr;
+    try {
+        std::string why;
+        TTM_REQUIRE(out && d_field, E_INVALID_ARG, "null pointer argument");
+        TTM_REQUIRE(params_ok(params, why), E_INVALID_ARG, why);
+        TTM_REQUIRE(params->dprime == 3, E_UNSUPPORTED, "the GPU path is built for d' = 3");
+        TTM_REQUIRE(precision == TTM_PREC_FP32, E_UNSUPPORTED, "only FP32 spectra are built in this version");
+        TTM_REQUIRE(tz > 0 && ty > 0 && tx > 0, E_SHAPE, "bad template shape");
+        TTM_REQUIRE(mask_fits(tz, params) && mask_fits(ty, params) && mask_fits(tx, params), E_INVALID_ARG,
+                    "mask radius (+ soft width) must fit symmetrically inside the template grid");
+        TTM_CUDA_TRY(cudaSetDevice(ctx->device));
+        P = new ttm_plan();
+        P->ctx = ctx;
+        P->fp = *params;
+        P->K = ttm_num_components(params->order_n, params->dprime);
+        P->prec = precision;
+        prep_create(ctx, P->prep, Z, Y, X, tz, ty, tx, *params);
+        plan_build_spectra(P, d_field);
+        const int64_t Vh = (int64_t)Z * Y * P->prep.Xh;
+        P->work.alloc(P->K * Vh * sizeof(float2));
+        const int64_t V = (int64_t)Z * Y * X;
+        P->cand_cap = V / 8 + 64;  // strict 26-neighbour maxima are >= 2 apart per axis
+        P->cand.alloc(P->cand_cap * (sizeof(int64_t) + sizeof(float)));
+        P->cand_count.alloc(sizeof(unsigned long long));
+        *out = P;
+        return TTM_OK;
+    } catch (const Error& e) {
+        delete P;
+        return (ttm_status)fail(ctx, e);
+    }
+}
+
+extern "C" void ttm_plan_destroy(ttm_plan* plan) { delete plan; }
+
+extern "C" int ttm_plan_components(const ttm_plan* plan) { return plan ? plan->K : 0; }
+
+extern "C" void ttm_plan_valid_box(const ttm_plan* plan, int* b)
+{
+    if (!plan || !b) return;
+    const Prep& p = plan->prep;
+    b[0] = p.tz / 2; b[1] = p.Z - (p.tz - p.tz / 2) + 1;
+    b[2] = p.ty / 2; b[3] = p.Y - (p.ty - p.ty / 2) + 1;
+    b[4] = p.tx / 2; b[5] = p.X - (p.tx - p.tx / 2) + 1;
+}
+
+extern "C" ttm_status ttm_correlate(ttm_plan* plan, const float* d_tomo, float* d_C, void* stream)
+{
+    if (!plan) return TTM_E_INVALID_ARG;
+    try {
+        TTM_REQUIRE(d_tomo && d_C, E_INVALID_ARG, "null pointer argument");
+        TTM_CUDA_TRY(cudaSetDevice(plan->ctx->device));
+        correlate_run(plan, d_tomo, d_C, (cudaStream_t)stream);
+        return TTM_OK;
+    } catch (const Error& e) {
+        return (ttm_status)fail(plan->ctx, e);
+    }
+}
+
+extern "C" ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream)
+{
+    if (!plan) return TTM_E_INVALID_ARG;
+    try {
+        TTM_REQUIRE(d_w, E_INVALID_ARG, "null pointer argument");
+        const Prep& p = plan->prep;
+        TTM_CUDA_TRY(cudaMemcpyAsync(d_w, p.w.p, (size_t)p.Z * p.Y * p.X * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        return TTM_OK;
+    } catch (const Error& e) {
+        return (ttm_status)fail(plan->ctx, e);
+    }
+}

@@ -1,0 +1,95 @@
+// ttm_internal.h -- context and plan objects behind the C ABI of include/ttm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ttm.h"
+#include "fft.cuh"
+
+namespace ttm {
+
+// Device buffer owned by a context or plan (freed in the destructor).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void alloc(size_t n);
+    void release();
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Per-tomogram-shape workspace shared by the TTM correlate and the TM
+// baseline: filtered tomogram, its spectrum, FP64 local sums and w.
+struct Prep {
+    int Z = 0, Y = 0, X = 0, Xh = 0;
+    int tz = 0, ty = 0, tx = 0;
+    double M = 0;              // sum of the mask
+    double filter_a = 0.2;
+    int64_t nblk_pre = 0;      // blocks of the prefilter reduction
+    DevBuf g32;                // float [Z][Y][X] filtered tomogram g
+    DevBuf G;                  // float2 [Z][Y][Xh] spectrum of g
+    DevBuf zc;                 // double2 [Z][Y][X]: (g, g^2), transformed in place
+    DevBuf mhat;               // double [(Z/2+1)][(Y/2+1)][(X/2+1)] mask spectrum / V
+    DevBuf w;                  // float [Z][Y][X] local normaliser
+    DevBuf partials;           // double [2][nblk_pre]
+    DevBuf floor;              // double [1]: variance floor
+    DevBuf mask_t;             // double [tz][ty][tx] mask on the template grid
+    LenPlan px32, py32, pz32, px64, py64, pz64;
+};
+
+void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
+                 const ttm_field_params& fp);
+// the three parts of the per-tomogram preparation, in this order:
+// g = h * f (+ variance floor), G = FFT(g), FP64 local sums -> w
+void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st);
+void prep_spectrum(Prep& p, cudaStream_t st);
+void prep_localsums(Prep& p, cudaStream_t st);
+
+// CUDA-event stage timing of a plan (no-ops while timing is off)
+enum Stage { ST_FILTER = 0, ST_SPECTRUM, ST_LOCALSUM, ST_ZCORR, ST_YPASS, ST_XPASS, ST_PEAKMAP, ST_COUNT };
+void stage_begin(ttm_plan* P, cudaStream_t st);
+void stage_end(ttm_plan* P, int stage, cudaStream_t st);
+
+// host mask on the template grid (Sec. 2 after Eq. 3); returns M
+double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<double>& m);
+
+}  // namespace ttm
+
+struct ttm_ctx {
+    int device = 0;
+    std::string last_error;
+    ttm::TwiddleCache twiddles;
+    int num_sms = 0;
+};
+
+struct ttm_plan {
+    ttm_ctx* ctx = nullptr;
+    ttm_field_params fp{};
+    int K = 0;
+    ttm_precision prec = TTM_PREC_FP32;
+    ttm::Prep prep;
+    ttm::DevBuf spec;        // [K][tz][Y][Xh] partial template spectra (x,y transformed)
+    ttm::DevBuf spec_scale;  // float [K] (reduced-precision spectra)
+    ttm::DevBuf work;        // float2 [K][Z][Y][Xh]
+    ttm::DevBuf cand;        // peak candidates
+    ttm::DevBuf cand_count;  // unsigned long long [1]
+    int64_t cand_cap = 0;
+    // stage timing
+    bool timing = false;
+    cudaEvent_t open_ev = nullptr;
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> free_ev;
+    ~ttm_plan();
+};
+
+namespace ttm {
+// set the context error text and return the code
+int fail(ttm_ctx* ctx, const Error& e);
+}

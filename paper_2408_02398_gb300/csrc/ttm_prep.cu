@@ -1,0 +1,288 @@
+// ttm_prep.cu -- per-tomogram preparation shared by TTM and TM:
+//   g = h * f (Eq. 3: separable taps [a, 1-2a, a], zero padded), in FP64,
+//   G = FFT(g) in FP32 (the image spectrum of Alg. 2),
+//   S1 = m * g and S2 = m^2 * g^2 (Eq. 2) by one packed FP64 complex FFT of
+//   g + i g^2 against the real, even spectrum of the mask, and
+//   w = 1 / sqrt(S2 - S1^2 / M) (0 at or below the variance floor).
+#include <cmath>
+#include <vector>
+
+#include "ttm_internal.h"
+
+namespace ttm {
+
+void DevBuf::alloc(size_t n)
+{
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        throw Error{E_OOM, "cudaMalloc(" + std::to_string(n) + " bytes) failed: " + cudaGetErrorString(e)};
+    }
+    bytes = n;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<double>& m)
+{
+    m.assign((size_t)tz * ty * tx, 0.0);
+    const int cz = tz / 2, cy = ty / 2, cx = tx / 2;
+    double M = 0;
+    for (int z = 0; z < tz; z++)
+        for (int y = 0; y < ty; y++)
+            for (int x = 0; x < tx; x++) {
+                double d = std::sqrt((double)(x - cx) * (x - cx) + (double)(y - cy) * (y - cy) +
+                                     (double)(z - cz) * (z - cz));
+                double v = 0.0;
+                if (d <= r) v = 1.0;
+                else if (soft > 0 && d < r + soft) v = 0.5 * (1.0 + std::cos(M_PI * (d - r) / soft));
+                m[((size_t)z * ty + y) * tx + x] = v;
+                M += v;
+            }
+    return M;
+}
+
+// ------------------------------------------------------------- kernels --
+
+constexpr int kPreThreads = 256;
+
+// one voxel per thread: g in FP64 from the 27-point product filter
+__global__ void __launch_bounds__(kPreThreads)
+k_prefilter(const float* __restrict__ f, int Z, int Y, int X, double a, float* __restrict__ g32,
+            double2* __restrict__ zc, double* __restrict__ partials, int64_t nblk)
+{
+    __shared__ double s1[kPreThreads], s2[kPreThreads];
+    const int64_t V = (int64_t)Z * Y * X;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double g = 0.0;
+    if (v < V) {
+        int x = (int)(v % X);
+        int64_t t = v / X;
+        int y = (int)(t % Y);
+        int z = (int)(t / Y);
+        const double tap[3] = {a, 1.0 - 2.0 * a, a};
+        for (int dz = -1; dz <= 1; dz++) {
+            int zz = z + dz;
+            if (zz < 0 || zz >= Z) continue;
+            for (int dy = -1; dy <= 1; dy++) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= Y) continue;
+                const float* row = f + ((int64_t)zz * Y + yy) * X;
+                double ty = tap[dz + 1] * tap[dy + 1];
+                for (int dx = -1; dx <= 1; dx++) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= X) continue;
+                    g += ty * tap[dx + 1] * (double)row[xx];
+                }
+            }
+        }
+        g32[v] = (float)g;
+        zc[v] = make_double2(g, g * g);
+    }
+    s1[threadIdx.x] = v < V ? g : 0.0;
+    s2[threadIdx.x] = v < V ? g * g : 0.0;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+            s2[threadIdx.x] += s2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s1[0];
+        partials[nblk + blockIdx.x] = s2[0];
+    }
+}
+
+// floor = 1e-12 * M * var(g), fixed summation order
+__global__ void __launch_bounds__(1024)
+k_var_floor(const double* __restrict__ partials, int64_t nblk, int64_t V, double M, double* floor_out)
+{
+    __shared__ double s1[1024], s2[1024];
+    double a = 0, b = 0;
+    for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) {
+        a += partials[i];
+        b += partials[nblk + i];
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+            s2[threadIdx.x] += s2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double mean = s1[0] / (double)V;
+        double var = s2[0] / (double)V - mean * mean;
+        floor_out[0] = 1e-12 * M * var;
+    }
+}
+
+// mask placed at the origin of the Z x Y x X grid (wrapped), as real rows
+struct SrcWrappedMask {
+    const double* m;
+    int Y, X, Z, tz, ty, tx;
+    __device__ double operator()(int64_t row, int x) const
+    {
+        int z = (int)(row / Y), y = (int)(row - (int64_t)z * Y);
+        int iz = wrap_to_template(z, Z, tz), iy = wrap_to_template(y, Y, ty), ix = wrap_to_template(x, X, tx);
+        if (iz < 0 || iy < 0 || ix < 0) return 0.0;
+        return m[((int64_t)iz * ty + iy) * tx + ix];
+    }
+};
+
+struct SrcFloat {
+    const float* g;
+    int X;
+    __device__ float operator()(int64_t row, int x) const { return g[row * X + x]; }
+};
+
+// real part / V of the (Hermitian half) mask spectrum on the octant
+// kz <= Z/2, ky <= Y/2, kx <= X/2 (the spectrum of a mask that is symmetric
+// in every axis is real and even in every axis)
+__global__ void k_mhat_octant(const double2* __restrict__ spec, int Z, int Y, int Xh, int X,
+                              double inv_V, double* __restrict__ oct)
+{
+    const int Zo = Z / 2 + 1, Yo = Y / 2 + 1, Xo = X / 2 + 1;
+    int64_t n = (int64_t)Zo * Yo * Xo;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int kx = (int)(i % Xo);
+        int64_t t = i / Xo;
+        int ky = (int)(t % Yo), kz = (int)(t / Yo);
+        oct[i] = spec[((int64_t)kz * Y + ky) * Xh + kx].x * inv_V;
+    }
+}
+
+// prologue of the inverse z pass: multiply by the mask spectrum
+struct ProMaskSpectrum {
+    const double* oct;
+    int Z, Y, X;
+    __device__ double2 operator()(double2 v, int64_t, int64_t i, int kz) const
+    {
+        int ky = (int)(i / X), kx = (int)(i - (int64_t)ky * X);
+        int az = kz <= Z - kz ? kz : Z - kz;
+        int ay = ky <= Y - ky ? ky : Y - ky;
+        int ax = kx <= X - kx ? kx : X - kx;
+        double m = oct[((int64_t)az * (Y / 2 + 1) + ay) * (X / 2 + 1) + ax];
+        return make_double2(v.x * m, v.y * m);
+    }
+};
+
+// epilogue of the inverse x pass: (S1, S2) -> w
+struct StoreW {
+    float* w;
+    const double* floor;
+    double M;
+    int X;
+    __device__ void operator()(double2 v, int64_t l, int64_t, int j) const
+    {
+        double S1 = v.x, S2 = v.y;
+        double var = S2 - S1 * S1 / M;
+        w[l * X + j] = var > floor[0] ? (float)(1.0 / sqrt(var)) : 0.0f;
+    }
+};
+
+// ---------------------------------------------------------------- host --
+
+void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
+                 const ttm_field_params& fp)
+{
+    TTM_REQUIRE(Z >= tz && Y >= ty && X >= tx, E_SHAPE, "tomogram smaller than the template");
+    TTM_REQUIRE(Z >= 2 && Y >= 2 && X >= 2, E_SHAPE, "each tomogram axis needs at least 2 voxels");
+    p.Z = Z; p.Y = Y; p.X = X; p.Xh = X / 2 + 1;
+    p.tz = tz; p.ty = ty; p.tx = tx;
+    p.filter_a = fp.filter_a;
+    p.px32 = make_len_plan(ctx->twiddles, X, false);
+    p.py32 = make_len_plan(ctx->twiddles, Y, false);
+    p.pz32 = make_len_plan(ctx->twiddles, Z, false);
+    p.px64 = make_len_plan(ctx->twiddles, X, true);
+    p.py64 = make_len_plan(ctx->twiddles, Y, true);
+    p.pz64 = make_len_plan(ctx->twiddles, Z, true);
+    const int64_t V = (int64_t)Z * Y * X, Vh = (int64_t)Z * Y * p.Xh;
+    p.nblk_pre = ceil_div(V, kPreThreads);
+    p.g32.alloc(V * sizeof(float));
+    p.G.alloc(Vh * sizeof(float2));
+    p.zc.alloc(V * sizeof(double2));
+    p.w.alloc(V * sizeof(float));
+    p.partials.alloc(2 * p.nblk_pre * sizeof(double));
+    p.floor.alloc(sizeof(double));
+    const int64_t noct = (int64_t)(Z / 2 + 1) * (Y / 2 + 1) * (X / 2 + 1);
+    p.mhat.alloc(noct * sizeof(double));
+
+    std::vector<double> m;
+    p.M = make_mask(tz, ty, tx, fp.mask_radius, fp.mask_soft_width, m);
+    TTM_REQUIRE(p.M > 0, E_INVALID_ARG, "mask is empty");
+    p.mask_t.alloc(m.size() * sizeof(double));
+    TTM_CUDA_TRY(cudaMemcpy(p.mask_t.p, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice));
+
+    // mask spectrum (FP64, once per plan): R2C rows, then y and z passes,
+    // using zc as the complex scratch
+    cudaStream_t st = 0;
+    double2* spec = p.zc.as<double2>();
+    SrcWrappedMask src{p.mask_t.as<double>(), Y, X, Z, tz, ty, tx};
+    launch_r2c_rows<double>(src, (int64_t)Z * Y, spec, p.px64, st);
+    launch_strided<double, -1>(spec, StridedAxis{p.Xh, Z, (int64_t)Y * p.Xh, p.Xh}, p.py64,
+                               ProIdentity<double>(), StoreTo<double>{spec, (int64_t)Y * p.Xh, p.Xh}, st);
+    launch_strided<double, -1>(spec, StridedAxis{(int64_t)Y * p.Xh, 1, 0, (int64_t)Y * p.Xh}, p.pz64,
+                               ProIdentity<double>(), StoreTo<double>{spec, 0, (int64_t)Y * p.Xh}, st);
+    k_mhat_octant<<<1024, 256, 0, st>>>(spec, Z, Y, p.Xh, X, 1.0 / (double)V, p.mhat.as<double>());
+    TTM_LAUNCH_CHECK();
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st)
+{
+    const int64_t V = (int64_t)p.Z * p.Y * p.X;
+    k_prefilter<<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, p.filter_a, p.g32.as<float>(),
+                                                           p.zc.as<double2>(), p.partials.as<double>(),
+                                                           p.nblk_pre);
+    TTM_LAUNCH_CHECK();
+    k_var_floor<<<1, 1024, 0, st>>>(p.partials.as<double>(), p.nblk_pre, V, p.M, p.floor.as<double>());
+    TTM_LAUNCH_CHECK();
+}
+
+// G = FFT(g): x (real-to-complex), y, z
+void prep_spectrum(Prep& p, cudaStream_t st)
+{
+    const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
+    float2* G = p.G.as<float2>();
+    launch_r2c_rows<float>(SrcFloat{p.g32.as<float>(), X}, (int64_t)Z * Y, G, p.px32, st);
+    launch_strided<float, -1>(G, StridedAxis{Xh, Z, (int64_t)Y * Xh, Xh}, p.py32, ProIdentity<float>(),
+                              StoreTo<float>{G, (int64_t)Y * Xh, Xh}, st);
+    launch_strided<float, -1>(G, StridedAxis{(int64_t)Y * Xh, 1, 0, (int64_t)Y * Xh}, p.pz32,
+                              ProIdentity<float>(), StoreTo<float>{G, 0, (int64_t)Y * Xh}, st);
+}
+
+// local sums in FP64: forward x, y, z of (g + i g^2), times the mask
+// spectrum, inverse z, y, x with the w epilogue
+void prep_localsums(Prep& p, cudaStream_t st)
+{
+    const int Z = p.Z, Y = p.Y, X = p.X;
+    double2* zc = p.zc.as<double2>();
+    const int64_t YX = (int64_t)Y * X;
+    launch_contig<double, -1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(), StoreTo<double>{zc, X, 1}, st);
+    launch_strided<double, -1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
+                               StoreTo<double>{zc, YX, X}, st);
+    launch_strided<double, -1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64, ProIdentity<double>(),
+                               StoreTo<double>{zc, 0, YX}, st);
+    launch_strided<double, +1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64,
+                               ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, StoreTo<double>{zc, 0, YX}, st);
+    launch_strided<double, +1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
+                               StoreTo<double>{zc, YX, X}, st);
+    launch_contig<double, +1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(),
+                              StoreW{p.w.as<float>(), p.floor.as<double>(), p.M, X}, st);
+}
+
+}  // namespace ttm

@@ -1,0 +1,293 @@
+"""Python binding of libttm (include/ttm.h): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls and takes
+PyTorch tensors for device buffers (PyTorch provides device memory and
+streams; every computation runs in the library's CUDA kernels). The library
+must have been built (``paper_2408_02398_gb300.build.build()``); importing
+this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libttm.so")
+
+TTM_OK = 0
+STATUS = {0: "TTM_OK", 1: "TTM_E_INVALID_ARG", 2: "TTM_E_SHAPE", 3: "TTM_E_UNSUPPORTED", 4: "TTM_E_OOM",
+          5: "TTM_E_CUDA", 6: "TTM_E_TIMEOUT", 7: "TTM_E_INTERNAL"}
+TTM_PREC_FP32, TTM_PREC_FP16_SPECTRA, TTM_PREC_BF16_SPECTRA = 0, 1, 2
+TTM_MAX_PLAIN, TTM_MAX_MLP_WARM = 0, 1
+
+# every symbol include/ttm.h declares
+EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_error", "ttm_num_components",
+           "ttm_version", "ttm_rotation_set", "ttm_build_tensor_field", "ttm_plan_create", "ttm_plan_destroy",
+           "ttm_plan_components", "ttm_plan_valid_box", "ttm_correlate", "ttm_plan_copy_w", "ttm_peak_map",
+           "ttm_find_peaks", "tm_correlate", "ttm_plan_enable_timing", "ttm_plan_stage_times", "ttm_num_stages",
+           "ttm_stage_name", "ttm_kernel_launches"]
+
+
+class TTMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(code, str(code)), msg))
+        self.code = code
+
+
+class ttm_field_params(C.Structure):
+    _fields_ = [("order_n", C.c_int), ("dprime", C.c_int), ("mask_radius", C.c_double),
+                ("mask_soft_width", C.c_double), ("filter_a", C.c_double), ("n_rot_base", C.c_int64),
+                ("cube_symmetrize", C.c_int)]
+
+
+_lib = None
+_vp = C.c_void_p
+_i = C.c_int
+_i64 = C.c_int64
+_d = C.c_double
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libttm.so is not built (run paper_2408_02398_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "ttm_default_params": (None, [C.POINTER(ttm_field_params)]),
+            "ttm_ctx_create": (_i, [_i, C.POINTER(_vp)]),
+            "ttm_ctx_destroy": (None, [_vp]),
+            "ttm_last_error": (C.c_char_p, [_vp]),
+            "ttm_num_components": (_i, [_i, _i]),
+            "ttm_version": (C.c_char_p, []),
+            "ttm_rotation_set": (_i, [_i64, _i, _vp]),
+            "ttm_build_tensor_field": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(ttm_field_params), _vp, _vp]),
+            "ttm_plan_create": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(ttm_field_params), _i, _i, _i, _i,
+                                     C.POINTER(_vp)]),
+            "ttm_plan_destroy": (None, [_vp]),
+            "ttm_plan_components": (_i, [_vp]),
+            "ttm_plan_valid_box": (None, [_vp, C.POINTER(_i)]),
+            "ttm_correlate": (_i, [_vp, _vp, _vp, _vp]),
+            "ttm_plan_copy_w": (_i, [_vp, _vp, _vp]),
+            "ttm_peak_map": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+            "ttm_find_peaks": (_i, [_vp, _vp, _i, _d, _vp, _vp, C.POINTER(_i), _vp]),
+            "tm_correlate": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _i, _i, C.POINTER(ttm_field_params), _vp, _i64,
+                                  _vp, _vp, _vp]),
+            "ttm_plan_enable_timing": (_i, [_vp, _i]),
+            "ttm_plan_stage_times": (_i, [_vp, _vp, _i]),
+            "ttm_num_stages": (_i, []),
+            "ttm_stage_name": (C.c_char_p, [_i]),
+            "ttm_kernel_launches": (C.c_uint64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------ marshalling --
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _dev(t, dtype, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(code, ctx=None):
+    if code != TTM_OK:
+        msg = lib().ttm_last_error(ctx).decode() if ctx else ""
+        raise TTMError(code, msg)
+
+
+def params(order_n=4, mask_radius=16.0, dprime=3, mask_soft_width=0.0, filter_a=0.2, n_rot_base=2048,
+           cube_symmetrize=True) -> ttm_field_params:
+    p = ttm_field_params()
+    lib().ttm_default_params(C.byref(p))
+    p.order_n, p.dprime, p.mask_radius = order_n, dprime, float(mask_radius)
+    p.mask_soft_width, p.filter_a = float(mask_soft_width), float(filter_a)
+    p.n_rot_base, p.cube_symmetrize = int(n_rot_base), int(bool(cube_symmetrize))
+    return p
+
+
+# -------------------------------------------------------- entry points --
+
+def ttm_num_components(order_n: int, dprime: int = 3) -> int:
+    return lib().ttm_num_components(order_n, dprime)
+
+
+def ttm_version() -> str:
+    return lib().ttm_version().decode()
+
+
+def ttm_rotation_set(n_base: int, cube: bool = True) -> np.ndarray:
+    q = np.zeros((n_base * (24 if cube else 1), 4))
+    _check(lib().ttm_rotation_set(n_base, int(cube), q.ctypes.data))
+    return q
+
+
+class Context:
+    """ttm_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        code = lib().ttm_ctx_create(device, C.byref(h))
+        if code != TTM_OK:
+            raise TTMError(code, "ttm_ctx_create(%d)" % device)
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ttm_ctx_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def check(self, code):
+        _check(code, self.h)
+
+
+def ttm_ctx_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def ttm_build_tensor_field(ctx: Context, d_tmpl, p: ttm_field_params, d_field, stream=None):
+    import torch
+    tz, ty, tx = d_tmpl.shape
+    ctx.check(lib().ttm_build_tensor_field(ctx.h, _dev(d_tmpl, torch.float32, "d_tmpl"), tz, ty, tx, C.byref(p),
+                                           _dev(d_field, torch.float64, "d_field"), _stream(stream)))
+
+
+class Plan:
+    """ttm_plan: a tensor field bound to one tomogram shape."""
+
+    def __init__(self, ctx: Context, d_field, p: ttm_field_params, shape, precision=TTM_PREC_FP32):
+        import torch
+        K, tz, ty, tx = d_field.shape
+        Z, Y, X = shape
+        h = _vp()
+        ctx.check(lib().ttm_plan_create(ctx.h, _dev(d_field, torch.float64, "d_field"), tz, ty, tx, C.byref(p),
+                                        Z, Y, X, precision, C.byref(h)))
+        self.h, self.ctx, self.shape, self.K = h, ctx, (Z, Y, X), lib().ttm_plan_components(h)
+        self.tshape = (tz, ty, tx)
+        self.params = p
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ttm_plan_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def valid_box(self):
+        b = (C.c_int * 6)()
+        lib().ttm_plan_valid_box(self.h, b)
+        return tuple(b)
+
+
+def ttm_plan_create(ctx, d_field, p, shape, precision=TTM_PREC_FP32) -> Plan:
+    return Plan(ctx, d_field, p, shape, precision)
+
+
+def ttm_correlate(plan: Plan, d_tomo, d_C, stream=None):
+    import torch
+    plan.ctx.check(lib().ttm_correlate(plan.h, _dev(d_tomo, torch.float32, "d_tomo"),
+                                       _dev(d_C, torch.float32, "d_C"), _stream(stream)))
+
+
+def ttm_plan_copy_w(plan: Plan, d_w, stream=None):
+    import torch
+    plan.ctx.check(lib().ttm_plan_copy_w(plan.h, _dev(d_w, torch.float32, "d_w"), _stream(stream)))
+
+
+def ttm_peak_map(plan: Plan, d_C, d_score, d_orient, d_frob=None, mode=TTM_MAX_PLAIN, mlp=None, stream=None):
+    import torch
+    plan.ctx.check(lib().ttm_peak_map(plan.h, _dev(d_C, torch.float32, "d_C"), mode, mlp,
+                                      _dev(d_score, torch.float32, "d_score"),
+                                      _dev(d_orient, torch.float32, "d_orient"),
+                                      None if d_frob is None else _dev(d_frob, torch.float32, "d_frob"),
+                                      _stream(stream)))
+
+
+def ttm_find_peaks(plan: Plan, d_map, P: int, min_dist: float, stream=None):
+    import torch
+    idx = np.zeros(max(P, 1), dtype=np.int64)
+    val = np.zeros(max(P, 1), dtype=np.float32)
+    n = C.c_int(0)
+    plan.ctx.check(lib().ttm_find_peaks(plan.h, _dev(d_map, torch.float32, "d_map"), P, float(min_dist),
+                                        idx.ctypes.data, val.ctypes.data, C.byref(n), _stream(stream)))
+    return idx[:n.value], val[:n.value]
+
+
+def tm_correlate(ctx: Context, d_tomo, d_tmpl, p: ttm_field_params, quats: np.ndarray, d_best, d_best_idx,
+                 stream=None):
+    import torch
+    Z, Y, X = d_tomo.shape
+    tz, ty, tx = d_tmpl.shape
+    q = np.ascontiguousarray(quats, dtype=np.float64).reshape(-1, 4)
+    ctx.check(lib().tm_correlate(ctx.h, _dev(d_tomo, torch.float32, "d_tomo"), Z, Y, X,
+                                 _dev(d_tmpl, torch.float32, "d_tmpl"), tz, ty, tx, C.byref(p), q.ctypes.data,
+                                 q.shape[0], _dev(d_best, torch.float32, "d_best"),
+                                 _dev(d_best_idx, torch.int32, "d_best_idx"), _stream(stream)))
+
+
+def ttm_plan_enable_timing(plan: Plan, on: bool = True):
+    plan.ctx.check(lib().ttm_plan_enable_timing(plan.h, int(on)))
+
+
+def ttm_plan_stage_times(plan: Plan) -> dict:
+    n = lib().ttm_num_stages()
+    ms = np.zeros(n)
+    plan.ctx.check(lib().ttm_plan_stage_times(plan.h, ms.ctypes.data, n))
+    return {lib().ttm_stage_name(i).decode(): float(ms[i]) for i in range(n)}
+
+
+def ttm_kernel_launches() -> int:
+    return int(lib().ttm_kernel_launches())
+
+
+# ------------------------------------------------------------ pipeline --
+
+class Matcher:
+    """Convenience: one template, one tomogram shape, device buffers for the
+    whole hot path (C, score, orientation, Frobenius)."""
+
+    def __init__(self, ctx: Context, template, p: ttm_field_params, shape, device="cuda"):
+        import torch
+        self.ctx, self.p = ctx, p
+        t = torch.as_tensor(np.ascontiguousarray(template, dtype=np.float32), device=device)
+        K = ttm_num_components(p.order_n, p.dprime)
+        self.field = torch.empty((K,) + tuple(t.shape), dtype=torch.float64, device=device)
+        ttm_build_tensor_field(ctx, t, p, self.field)
+        torch.cuda.synchronize()
+        self.plan = Plan(ctx, self.field, p, shape)
+        Z, Y, X = shape
+        self.C = torch.empty((K, Z, Y, X), dtype=torch.float32, device=device)
+        self.score = torch.empty((Z, Y, X), dtype=torch.float32, device=device)
+        self.orient = torch.empty((3, Z, Y, X), dtype=torch.float32, device=device)
+        self.frob = torch.empty((Z, Y, X), dtype=torch.float32, device=device)
+
+    def run(self, d_tomo, stream=None):
+        ttm_correlate(self.plan, d_tomo, self.C, stream)
+        ttm_peak_map(self.plan, self.C, self.score, self.orient, self.frob, stream=stream)
+        return self.score, self.orient, self.frob

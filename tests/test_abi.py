@@ -1,0 +1,79 @@
+"""The C-ABI library loads without a GPU and exports every symbol that
+include/ttm.h declares; host-only entry points agree with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02398_gb300 import build as B
+from paper_2408_02398_gb300 import ttm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ttm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:ttm|tm)_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = header_functions()
+    assert len(names) >= 15
+    L = ttm.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(ttm.EXPORTS) == names
+
+
+def test_status_codes_match_header():
+    src = open(os.path.join(ROOT, "include", "ttm.h")).read()
+    codes = dict((m[0], int(m[1])) for m in re.findall(r"(TTM_(?:OK|E_[A-Z_]+))\s*=\s*(\d+)", src))
+    assert {v: k for k, v in codes.items()} == ttm.STATUS
+    common = open(os.path.join(ROOT, "paper_2408_02398_gb300", "csrc", "ttm_common.cuh")).read()
+    for name, val in codes.items():
+        short = name.replace("TTM_", "")
+        assert re.search(r"\b%s\s*=\s*%d\b" % (short, val), common), name
+
+
+def test_component_counts():
+    for n in (2, 4, 6):
+        for d in (3, 4):
+            assert ttm.ttm_num_components(n, d) == O.num_components(n, d)
+
+
+def test_default_params():
+    p = ttm.params()
+    assert p.filter_a == pytest.approx(0.2)   # Sec. 2: a = 1/5
+    assert p.order_n == 4 and p.dprime == 3 and p.cube_symmetrize == 1
+
+
+@pytest.mark.parametrize("cube", [False, True])
+def test_rotation_set_equals_oracle_set(cube):
+    """The library's quadrature is the same set of rotations as the
+    oracle's (written independently; order and quaternion sign may differ)."""
+    q_lib = ttm.ttm_rotation_set(40, cube)
+    q_or = O.rotation_set(40, cube=cube)
+    assert q_lib.shape == q_or.shape
+    assert np.allclose(np.linalg.norm(q_lib, axis=1), 1.0)
+
+    def key(q):
+        R = O.quat_to_rot(q)
+        return tuple(np.round(R.ravel(), 9))
+
+    assert sorted(map(key, q_lib)) == sorted(map(key, q_or))
+    if not cube:
+        assert np.allclose(q_lib, q_or, atol=1e-14)
+
+
+def test_rotation_set_rejects_bad_args():
+    L = ttm.lib()
+    assert L.ttm_rotation_set(0, 1, None) == 1
+    assert L.ttm_rotation_set(4, 1, None) == 1

@@ -1,0 +1,305 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs, element by element, at sizes
+that span several tiles and leave ragged tails.
+
+Tolerances: C maps max abs error <= 2e-5 (FP32 FFT correlation of values
+|C| <= 1), w relative 1e-5, score abs error <= 1e-4 (FP32), orientation <=
+1 degree where the maximum is well separated (best minus second-best
+distinct local maximum > 1e-3 |s|), peak lists bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02398_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C_TOL = 2e-5
+S_TOL = 1e-4
+ANG_TOL_DEG = 1.0
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_02398_gb300 import build
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    return ttm
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.Context(0)
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def oracle_field(tmpl, r, n, n_base):
+    m, _ = O.mask(tmpl.shape, r)
+    tp, _ = O.normalise_template(tmpl, m)
+    return O.tensor_field(tp, O.rotation_set(n_base), n, 3)
+
+
+def angle_deg(u, v):
+    d = np.clip(np.abs(np.sum(u * v, axis=-1)), 0, 1)
+    return np.degrees(np.arccos(d))
+
+
+# ------------------------------------------------------------- field --
+
+@pytest.mark.parametrize("N,r,n", [(9, 3.0, 2), (16, 7.0, 4), (11, 4.0, 6)])
+def test_tensor_field_matches_oracle(T, ctx, N, r, n):
+    tmpl = synth.gaussian_blob_template(N, seed=100 + N)
+    p = T.params(order_n=n, mask_radius=r, n_rot_base=32)
+    K = T.ttm_num_components(n)
+    d_field = torch.empty((K, N, N, N), dtype=torch.float64, device="cuda")
+    T.ttm_build_tensor_field(ctx, dev(tmpl), p, d_field)
+    torch.cuda.synchronize()
+    ref = oracle_field(tmpl, r, n, 32)
+    got = d_field.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# --------------------------------------------------------- correlate --
+
+CASES = [
+    # shape (Z, Y, X), template N, r, n
+    ((24, 20, 28), 7, 3.0, 2),
+    ((21, 20, 28), 8, 3.0, 4),
+    ((32, 30, 36), 9, 4.0, 6),
+    ((9, 9, 10), 9, 4.0, 2),      # volume as small as the template (one valid voxel row)
+]
+
+
+def run_gpu(T, ctx, tomo, field, p):
+    plan = T.Plan(ctx, dev(field, torch.float64), p, tomo.shape)
+    K = field.shape[0]
+    d_C = torch.empty((K,) + tomo.shape, dtype=torch.float32, device="cuda")
+    T.ttm_correlate(plan, dev(tomo), d_C)
+    d_w = torch.empty(tomo.shape, dtype=torch.float32, device="cuda")
+    T.ttm_plan_copy_w(plan, d_w)
+    d_s = torch.empty(tomo.shape, dtype=torch.float32, device="cuda")
+    d_u = torch.empty((3,) + tomo.shape, dtype=torch.float32, device="cuda")
+    d_F = torch.empty(tomo.shape, dtype=torch.float32, device="cuda")
+    T.ttm_peak_map(plan, d_C, d_s, d_u, d_F)
+    torch.cuda.synchronize()
+    return plan, d_C, d_w, d_s, d_u, d_F
+
+
+@pytest.mark.parametrize("shape,N,r,n", CASES)
+def test_correlate_periodic_all_voxels(T, ctx, shape, N, r, n):
+    """C and w on the whole grid against the oracle's periodic direct sums."""
+    tomo = synth.normals(7 + N, 1, int(np.prod(shape))).reshape(shape).astype(np.float32)
+    tmpl = synth.gaussian_blob_template(N, seed=N)
+    field = oracle_field(tmpl, r, n, 16)
+    p = T.params(order_n=n, mask_radius=r, n_rot_base=16)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p)
+    pr = O.Prepared(tomo.astype(np.float64), tmpl, r)
+    w, _, _ = O.local_w(pr.g, pr.m, None, periodic=True, floor=pr.floor)
+    Cref = O.correlate(pr.g, field, None, periodic=True, w=w)
+    got_w = d_w.cpu().numpy().ravel()
+    assert np.abs(got_w - w).max() <= 1e-5 * np.abs(w).max()
+    got = d_C.cpu().numpy().reshape(field.shape[0], -1)
+    assert np.abs(got - Cref).max() <= C_TOL * max(1.0, np.abs(Cref).max())
+    # Frobenius proxy
+    F = O.frobenius(Cref, n)
+    assert np.abs(d_F.cpu().numpy().ravel() - F).max() <= C_TOL * max(1.0, F.max()) * 3
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_peak_map_random_tensors(T, ctx, n):
+    """Maximiser on normalised random tensors: score within 1e-4 of the
+    oracle's dense-sampling + Newton maximum at every voxel."""
+    K = T.ttm_num_components(n)
+    shape = (4, 50, 50)
+    V = int(np.prod(shape))
+    C = synth.random_tensors(1000 + n, V, K).T.copy()      # [K][V]
+    C /= O.frobenius(C, n)[None, :]                        # ||C||_F = 1
+    tmpl = synth.gaussian_blob_template(3, seed=1)
+    field = oracle_field(tmpl, 1.0, n, 4)
+    p = T.params(order_n=n, mask_radius=1.0, n_rot_base=4)
+    plan = T.Plan(ctx, dev(field, torch.float64), p, shape)
+    d_s = torch.empty(shape, dtype=torch.float32, device="cuda")
+    d_u = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+    d_F = torch.empty(shape, dtype=torch.float32, device="cuda")
+    T.ttm_peak_map(plan, dev(C.reshape((K,) + shape)), d_s, d_u, d_F)
+    torch.cuda.synchronize()
+    sv = np.arange(V)[:: max(1, V // 3000)]
+    s, u, sec = O.maximise(C[:, sv], n, 3, nsamples=20000)
+    gs = d_s.cpu().numpy().ravel()[sv]
+    gu = d_u.cpu().numpy().reshape(3, -1)[:, sv].T
+    err = np.abs(gs - s)
+    assert err.max() <= S_TOL, (err.max(), int((err > S_TOL).sum()))
+    sep = (s - sec) > 1e-3 * np.abs(s)
+    assert angle_deg(gu[sep], u[sep]).max() <= ANG_TOL_DEG
+    assert np.all(gu[:, 2] >= 0)
+    assert np.abs(d_F.cpu().numpy().ravel() - 1.0).max() < 1e-5
+
+
+def test_degenerate_inputs(T, ctx):
+    """Constant tomogram: zero local variance -> w = 0 -> C = 0, score 0."""
+    shape = (16, 16, 20)
+    tmpl = synth.gaussian_blob_template(7, seed=3)
+    field = oracle_field(tmpl, 3.0, 2, 4)
+    p = T.params(order_n=2, mask_radius=3.0, n_rot_base=4)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, np.full(shape, 2.5, np.float32), field, p)
+    box = plan.valid_box()
+    w = d_w.cpu().numpy()[box[0]:box[1], box[2]:box[3], box[4]:box[5]]
+    assert np.all(w == 0)
+    assert np.all(d_s.cpu().numpy()[box[0]:box[1], box[2]:box[3], box[4]:box[5]] == 0)
+
+
+def test_errors_are_reported(T, ctx):
+    tmpl = synth.gaussian_blob_template(7, seed=3)
+    field = dev(oracle_field(tmpl, 3.0, 2, 4), torch.float64)
+    p = T.params(order_n=2, mask_radius=3.0, n_rot_base=4)
+    with pytest.raises(T.TTMError) as e:
+        T.Plan(ctx, field, p, (17, 16, 16))          # 17 is not 7-smooth
+    assert e.value.code == 2
+    with pytest.raises(T.TTMError) as e:
+        T.Plan(ctx, field, p, (6, 16, 16))           # smaller than the template
+    assert e.value.code == 2
+    with pytest.raises(T.TTMError) as e:
+        T.Plan(ctx, field, T.params(order_n=2, mask_radius=3.0, dprime=4), (16, 16, 16))
+    assert e.value.code == 3
+    with pytest.raises(T.TTMError) as e:
+        T.Plan(ctx, field, T.params(order_n=2, mask_radius=3.5), (16, 16, 16))  # mask does not fit 7^3
+    assert e.value.code == 1
+    L = T.lib()
+    assert L.ttm_correlate(None, None, None, None) == 1
+
+
+# -------------------------------------------------------------- TM --
+
+def test_tm_matches_oracle(T, ctx):
+    shape = (20, 21, 24)
+    N, r = 7, 3.0
+    tomo = synth.normals(55, 1, int(np.prod(shape))).reshape(shape).astype(np.float32)
+    tmpl = synth.gaussian_blob_template(N, seed=55)
+    quats = np.vstack([O.cube_rotations()[:6], synth.shoemake_quats(synth.uniforms(55, 9, 6))])
+    p = T.params(order_n=2, mask_radius=r)
+    d_best = torch.empty(shape, dtype=torch.float32, device="cuda")
+    d_idx = torch.empty(shape, dtype=torch.int32, device="cuda")
+    T.tm_correlate(ctx, dev(tomo), dev(tmpl), p, quats, d_best, d_idx)
+    torch.cuda.synchronize()
+    pr = O.Prepared(tomo.astype(np.float64), tmpl, r)
+    w, _, _ = O.local_w(pr.g, pr.m, None, periodic=True, floor=pr.floor)
+    best, idx = O.tm(pr.g, pr.tp, quats, None, periodic=True, w=w)
+    gb = d_best.cpu().numpy().ravel()
+    gi = d_idx.cpu().numpy().ravel()
+    assert np.abs(gb - best).max() <= C_TOL
+    # the arg-max index is unique wherever the best two rotations differ clearly
+    allc = np.stack([O.correlate(pr.g, O.rotate_template(pr.tp, q)[None], None, True, w)[0] for q in quats])
+    srt = np.sort(allc, axis=0)
+    clear = (srt[-1] - srt[-2]) > 1e-4
+    assert np.array_equal(gi[clear], idx[clear])
+
+
+def test_tm_finds_planted_copy_with_lncc_one(T, ctx):
+    """A copy of the template rotated by a quarter-turn, alone in a zero
+    volume, gives LNCC 1 at its centre for that rotation (Eqs. 1-5)."""
+    N, r = 9, 4.0
+    tmpl = synth.gaussian_blob_template(N, seed=77)
+    s = math.sqrt(0.5)
+    quats = np.array([[1, 0, 0, 0], [s, 0, 0, s], [s, 0, 0, -s], [0, 1, 0, 0.0]])
+    vol = np.zeros((24, 24, 28), np.float32)
+    rot = O.rotate_template(tmpl, quats[1]).astype(np.float32)
+    c0 = (12, 11, 13)
+    h = N // 2
+    vol[c0[0] - h:c0[0] + h + 1, c0[1] - h:c0[1] + h + 1, c0[2] - h:c0[2] + h + 1] = rot
+    p = T.params(order_n=2, mask_radius=r)
+    d_best = torch.empty(vol.shape, dtype=torch.float32, device="cuda")
+    d_idx = torch.empty(vol.shape, dtype=torch.int32, device="cuda")
+    T.tm_correlate(ctx, dev(vol), dev(tmpl), p, quats, d_best, d_idx)
+    torch.cuda.synchronize()
+    assert d_idx[c0].item() == 1
+    assert abs(d_best[c0].item() - 1.0) < 1e-4
+
+
+# ----------------------------------------------------- find peaks --
+
+def test_find_peaks_host_logic_bit_exact(T, ctx):
+    shape = (20, 24, 28)
+    rng = np.random.default_rng(5)
+    s = rng.random(shape).astype(np.float32)
+    s[5:8, 5:8, 5:8] = 2.0     # a plateau: one peak at its lowest index
+    tmpl = synth.gaussian_blob_template(5, seed=1)
+    field = oracle_field(tmpl, 2.0, 2, 4)
+    plan = T.Plan(ctx, dev(field, torch.float64), T.params(order_n=2, mask_radius=2.0, n_rot_base=4), shape)
+    box = plan.valid_box()
+    for P, md in [(10, 4.0), (50, 2.5), (0, 1.0), (1000, 1.0)]:
+        gi, gv = T.ttm_find_peaks(plan, dev(s), P, md)
+        oi, ov = O.find_peaks(s.astype(np.float64), box, P, md)
+        assert np.array_equal(gi, oi)
+        assert np.array_equal(gv.astype(np.float64), ov)
+
+
+# ------------------------------------------------------- end to end --
+
+@pytest.fixture(scope="module")
+def small(T, ctx):
+    """64^3 white noise, 16^3 six-Gaussian template, r = 7, n = 2, four copies
+    at amplitude 0.5; GPU path with its own field, oracle with its own."""
+    wl = synth.workload_small()
+    p = T.params(order_n=2, mask_radius=wl.mask_radius, n_rot_base=2048)
+    m = T.Matcher(ctx, wl.template, p, wl.tomo.shape)
+    m.run(dev(wl.tomo))
+    torch.cuda.synchronize()
+    res = O.ttm(wl.tomo, wl.template, wl.mask_radius, 2, O.rotation_set(2048))
+    return wl, m, res
+
+
+def test_small_workload_field(T, small):
+    wl, m, res = small
+    got = m.field.cpu().numpy()
+    assert np.abs(got - res["T"]).max() <= 1e-12 * np.abs(res["T"]).max()
+
+
+def test_small_workload_maps(T, small):
+    wl, m, res = small
+    v = res["vox"]
+    K = res["C"].shape[0]
+    gC = m.C.cpu().numpy().reshape(K, -1)[:, v]
+    assert np.abs(gC - res["C"]).max() <= C_TOL
+    gs = m.score.cpu().numpy().ravel()[v]
+    assert np.abs(gs - res["score"]).max() <= S_TOL
+    gF = m.frob.cpu().numpy().ravel()[v]
+    assert np.abs(gF - res["F"]).max() <= C_TOL * 3
+    gu = m.orient.cpu().numpy().reshape(3, -1)[:, v].T
+    sep = (res["score"] - res["second"]) > 1e-3 * np.abs(res["score"])
+    assert angle_deg(gu[sep], res["orient"][sep]).max() <= ANG_TOL_DEG
+    # at the planted centres
+    Z, Y, X = wl.tomo.shape
+    pos = {int(x): i for i, x in enumerate(v)}
+    for c in wl.planted.centres:
+        i = pos[int((c[0] * Y + c[1]) * X + c[2])]
+        assert abs(gs[i] - res["score"][i]) <= S_TOL
+        assert angle_deg(gu[i], res["orient"][i]) <= ANG_TOL_DEG
+
+
+def test_small_workload_peaks(T, small):
+    """Top peaks of the GPU score and Frobenius maps equal the oracle's
+    wherever the ranking is not decided by less than the score tolerance."""
+    wl, m, res = small
+    Z, Y, X = wl.tomo.shape
+    box = m.plan.valid_box()
+    for key, gmap in (("score", m.score), ("F", m.frob)):
+        full = np.full(Z * Y * X, -np.inf)
+        full[res["vox"]] = res[key]
+        oi, ov = O.find_peaks(full.reshape(Z, Y, X), box, 12, 2 * wl.mask_radius)
+        gi, gv = T.ttm_find_peaks(m.plan, gmap, 12, 2 * wl.mask_radius)
+        # compare the prefix of peaks separated from their successors by > 2 tol
+        k = len(ov)
+        for j in range(len(ov) - 1):
+            if ov[j] - ov[j + 1] <= 2 * S_TOL:
+                k = j
+                break
+        assert k >= 3
+        assert np.array_equal(gi[:k], oi[:k]), (key, gi[:k], oi[:k])
