@@ -58,13 +58,14 @@ def _declare(L):
         "oracle_rotate_template": (None, [_pd, _i, _i, _i, _pd, _pd]),
         "oracle_tensor_field": (_i, [_pd, _i, _i, _i, _pd, _i64, _i, _i, _pd]),
         "oracle_global_variance": (_d, [_pd, _i64]),
+        "oracle_mean_square": (_d, [_pd, _i64]),
         "oracle_local_w": (None, [_pd, _i, _i, _i, _pd, _i, _i, _i, _i, _d, _pi64, _i64, _pd,
                                   _pd, _pd]),
         "oracle_correlate": (None, [_pd, _i, _i, _i, _pd, _i, _i, _i, _i, _i, _pi64, _i64, _pd,
                                     _pd]),
         "oracle_frobenius": (None, [_pd, _i, _i, _i, _i64, _pd]),
         "oracle_sample_directions": (None, [_i, _i, _pd]),
-        "oracle_maximise": (None, [_pd, _i64, _i, _i, _i, _pd, _pd, _pd]),
+        "oracle_maximise": (None, [_pd, _i64, _i, _i, _i, _pd, _pd, _pd, _pd]),
         "oracle_poly_eval": (_d, [_pd, _i, _i, _pd, _pd, _pd]),
         "oracle_find_peaks": (_i, [_pd, _i, _i, _i, _i, _i, _i, _i, _i, _i, _i, _d, _pi64, _pd]),
         "oracle_tm": (None, [_pd, _i, _i, _i, _pd, _i, _i, _i, _pd, _i64, _i, _pi64, _i64, _pd,
@@ -210,9 +211,15 @@ def global_variance(g) -> float:
     return lib().oracle_global_variance(_p(g), g.size)
 
 
+def mean_square(g) -> float:
+    g = _f64(g)
+    return lib().oracle_mean_square(_p(g), g.size)
+
+
 def var_floor(g, M: float) -> float:
-    """Local variances at or below this give w = 0 (1e-12 * M * global var of g)."""
-    return 1e-12 * M * global_variance(g)
+    """Local variances at or below this give w = 0: 1e-12 * M * mean(g^2), the
+    level of an (almost) empty window relative to the volume's energy."""
+    return 1e-12 * M * mean_square(g)
 
 
 def _vox(vox, shape):
@@ -280,15 +287,20 @@ def sample_directions(d: int, ns: int) -> np.ndarray:
     return U
 
 
-def maximise(C, n: int, d: int = 3, nsamples: int = 20000):
+def maximise(C, n: int, d: int = 3, nsamples: int = 20000, with_curvature: bool = False):
     """Per voxel (columns of C = [K][nvox]): score max_u C.u^n, canonical
-    argmax u (nvox x d) and the best distinct second local maximum."""
+    argmax u (nvox x d) and the best distinct second local maximum; with
+    with_curvature also the curvature at the maximum (smallest eigenvalue of
+    minus the Riemannian Hessian)."""
     C = _f64(C)
     K, nv = C.shape
     s = np.zeros(nv)
     u = np.zeros((nv, d))
     sec = np.zeros(nv)
-    lib().oracle_maximise(_p(C), nv, n, d, nsamples, _p(s), _p(u), _p(sec))
+    curv = np.zeros(nv) if with_curvature else None
+    lib().oracle_maximise(_p(C), nv, n, d, nsamples, _p(s), _p(u), _p(sec), _p(curv))
+    if with_curvature:
+        return s, u, sec, curv
     return s, u, sec
 
 
@@ -354,8 +366,8 @@ def ttm(tomo, tmpl, r: float, n: int, quats, vox=None, periodic: bool = False, d
     out = {"vox": v, "w": w, "S1": S1, "S2": S2, "C": C, "T": T, "F": frobenius(C, n, d),
            "prepared": pr}
     if maximise_too:
-        s, u, sec = maximise(C, n, d, nsamples)
-        out.update(score=s, orient=u, second=sec)
+        s, u, sec, curv = maximise(C, n, d, nsamples, with_curvature=True)
+        out.update(score=s, orient=u, second=sec, curv=curv)
     return out
 
 

@@ -26,7 +26,8 @@
  *   - Alg. 1 (rotate t', no second S) is followed rather than Eq. 9's S(t')_R;
  *   - rotated copies are t'_R(p) = t'(R^T p), trilinear, zero outside the grid;
  *   - with d' = 3 the tensor weight of a rotation R is (R e_z)^{(x)n};
- *   - w(x) = 0 where the local variance is not above var_floor.
+ *   - w(x) = 0 where the local variance is not above var_floor (callers use
+ *     1e-12 * M * mean(g^2)) or not above 1e-10 * S2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -367,9 +368,11 @@ ORACLE_API int oracle_tensor_field(const double* tp, int tz, int ty, int tx, con
 /* Eq. 2: w(x) = 1 / sqrt(<S(tau_x f)^2, 1> - <S(tau_x f), 1>^2 / M) with
  * tau_x f(z) = f(z + x) and S = m (h * .): S1 = sum_p m(p) g(x+p),
  * S2 = sum_p m(p)^2 g(x+p)^2, var = S2 - S1^2 / M, where g = h * f is the
- * filtered tomogram. w = 0 where var <= var_floor. Evaluated at the voxels
- * listed in vox (linear indices); periodic != 0 wraps x+p around the grid,
- * otherwise samples outside the volume count as 0.                           */
+ * filtered tomogram. The local variance is taken as zero (w = 0) where it is
+ * not above var_floor or not above 1e-10 * S2, i.e. where the window is
+ * constant to about five digits. Evaluated at the voxels listed in vox
+ * (linear indices); periodic != 0 wraps x+p around the grid, otherwise
+ * samples outside the volume count as 0.                                     */
 
 static inline int wrap_or_out(long v, long n, int periodic, long* o)
 {
@@ -387,6 +390,13 @@ ORACLE_API double oracle_global_variance(const double* g, int64_t n)
     for (int64_t i = 0; i < n; i++) { s += g[i]; s2 += g[i] * g[i]; }
     double mean = s / (double)n;
     return s2 / (double)n - mean * mean;
+}
+
+ORACLE_API double oracle_mean_square(const double* g, int64_t n)
+{
+    double s2 = 0.0;
+    for (int64_t i = 0; i < n; i++) s2 += g[i] * g[i];
+    return s2 / (double)n;
 }
 
 ORACLE_API void oracle_local_w(const double* g, int Z, int Y, int X, const double* m, int tz, int ty,
@@ -415,7 +425,7 @@ ORACLE_API void oracle_local_w(const double* g, int Z, int Y, int X, const doubl
                     S2 += mv * mv * gv * gv;
                 }
         double var = S2 - S1 * S1 / M;
-        w[i] = var > var_floor ? 1.0 / sqrt(var) : 0.0;
+        w[i] = (var > var_floor && var > 1e-10 * S2) ? 1.0 / sqrt(var) : 0.0;
         if (S1out) S1out[i] = S1;
         if (S2out) S2out[i] = S2;
     }
@@ -692,11 +702,64 @@ ORACLE_API void oracle_sample_directions(int d, int ns, double* U)
 
 #define NNB 8
 
+/* smallest eigenvalue of a small symmetric matrix (m <= 3) by cyclic Jacobi
+ * rotations */
+static double min_eig_sym(double* A, int m)
+{
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) off += A[p * m + q] * A[p * m + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) {
+                double apq = A[p * m + q];
+                if (fabs(apq) < 1e-300) continue;
+                double th = 0.5 * atan2(2.0 * apq, A[q * m + q] - A[p * m + p]);
+                double c = cos(th), sn = sin(th);
+                for (int k = 0; k < m; k++) {
+                    double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - sn * akq;
+                    A[k * m + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < m; k++) {
+                    double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - sn * aqk;
+                    A[q * m + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double mn = A[0];
+    for (int i = 1; i < m; i++) if (A[i * m + i] < mn) mn = A[i * m + i];
+    return mn;
+}
+
+/* curvature of p at a maximiser u: the smallest eigenvalue of minus the
+ * Riemannian Hessian (tangent space) -- how sharply the maximum is defined */
+static double curvature_at(const poly_t* P, const double* C, const double* u)
+{
+    int d = P->d;
+    double p, gr[4], H[16], B[12], A[9];
+    poly_eval(P, C, u, &p, gr, H);
+    tangent_basis(u, d, B);
+    double ug = 0.0;
+    for (int i = 0; i < d; i++) ug += u[i] * gr[i];
+    for (int a = 0; a < d - 1; a++)
+        for (int b = 0; b < d - 1; b++) {
+            double s = 0.0;
+            for (int i = 0; i < d; i++)
+                for (int j = 0; j < d; j++) s += B[a * d + i] * H[i * d + j] * B[b * d + j];
+            if (a == b) s -= ug;
+            A[a * (d - 1) + b] = -s;
+        }
+    return min_eig_sym(A, d - 1);
+}
+
 /* For each voxel i: s[i] = max p, u[i*d..] = canonical argmax,
  * second[i] = the best value of a local maximum at least 1 degree away from
- * the argmax (or -inf), iters[i] = polish iterations of the winning start.  */
+ * the argmax (or -inf), curv[i] (if not NULL) = curvature at the argmax.     */
 ORACLE_API void oracle_maximise(const double* C, int64_t nvox, int n, int d, int nsamples,
-                                double* s, double* u, double* second)
+                                double* s, double* u, double* second, double* curv)
 {
     int K = oracle_num_components(n, d);
     int* alpha = (int*)malloc(sizeof(int) * K * d);
@@ -775,6 +838,7 @@ ORACLE_API void oracle_maximise(const double* C, int64_t nvox, int n, int d, int
             for (int i = 0; i < d; i++) dot += found_u[t][i] * ub[i];
             if (fabs(dot) < cos1 && found_p[t] > sec) sec = found_p[t];
         }
+        if (curv) curv[v] = curvature_at(&P, c, ub);
         canonicalise(ub, d);
         s[v] = best;
         for (int i = 0; i < d; i++) u[(size_t)v * d + i] = ub[i];

@@ -12,6 +12,7 @@
 // x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -107,6 +108,7 @@ struct SinkNormalise {
 void launch_zcorr(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
                   const LenPlan& pz, cudaStream_t st)
 {
+    if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, st)) return;
     const int Z = pz.L;
     const int ld = (Z % 2 == 0) ? Z + 1 : Z;
     int W = 16;
@@ -129,8 +131,8 @@ void plan_build_spectra(ttm_plan* P, const double* d_field)
     cudaStream_t st = 0;
     for (int a = 0; a < P->K; a++) {
         const double* Ta = d_field + (int64_t)a * tz * ty * tx;
-        launch_r2c_rows<double>(SrcFieldRows{Ta, Y, X, ty, tx}, (int64_t)tz * Y, scratch, p.px64, st);
-        launch_strided<double, -1>(scratch, StridedAxis{Xh, tz, (int64_t)Y * Xh, Xh}, p.py64,
+        launch_r2c_any<double>(SrcFieldRows{Ta, Y, X, ty, tx}, (int64_t)tz * Y, scratch, p.px64, st);
+        launch_strided_any<double, -1>(scratch, StridedAxis{Xh, tz, (int64_t)Y * Xh, Xh}, p.py64,
                                    ProIdentity<double>(), StoreTo<double>{scratch, (int64_t)Y * Xh, Xh}, st);
         k_spec_store<<<1024, 256, 0, st>>>(scratch, ncomp, 1.0 / (double)V, P->spec.as<float2>() + a * ncomp);
         TTM_LAUNCH_CHECK();
@@ -154,10 +156,10 @@ void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st
     float2* work = P->work.as<float2>();
     launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32, st);
     stage_end(P, ST_ZCORR, st);
-    launch_strided<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
+    launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                               StoreTo<float>{work, ncols, Xh}, st);
     stage_end(P, ST_YPASS, st);
-    launch_c2r_rows<float>(work, (int64_t)Z * Y, SinkNormalise{d_C, p.w.as<float>(), V, X}, p.px32, P->K, st);
+    launch_c2r_any<float>(work, (int64_t)Z * Y, SinkNormalise{d_C, p.w.as<float>(), V, X}, p.px32, P->K, st);
     stage_end(P, ST_XPASS, st);
 }
 

@@ -1,12 +1,14 @@
 // ttm_prep.cu -- per-tomogram preparation shared by TTM and TM:
-//   g = h * f (Eq. 3: separable taps [a, 1-2a, a], zero padded), in FP64,
+//   g = h * f (Eq. 3: separable taps [a, 1-2a, a], zero padded), FP32,
 //   G = FFT(g) in FP32 (the image spectrum of Alg. 2),
 //   S1 = m * g and S2 = m^2 * g^2 (Eq. 2) by one packed FP64 complex FFT of
 //   g + i g^2 against the real, even spectrum of the mask, and
-//   w = 1 / sqrt(S2 - S1^2 / M) (0 at or below the variance floor).
+//   w = 1 / sqrt(S2 - S1^2 / M) (0 where the local variance is zero to
+//   rounding: below 1e-12 M mean(g^2) or below 1e-10 S2).
 #include <cmath>
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -54,80 +56,68 @@ double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<doub
 
 constexpr int kPreThreads = 256;
 
-// one voxel per thread: g in FP64 from the 27-point product filter
+// One voxel per thread: g = h * f from the 27-point product filter in FP32
+// (the input is FP32), written as g (f32) and as (g, g^2) in FP64 for the
+// local sums; per-block partial sums of g^2 for the variance floor.
 __global__ void __launch_bounds__(kPreThreads)
-k_prefilter(const float* __restrict__ f, int Z, int Y, int X, double a, float* __restrict__ g32,
-            double2* __restrict__ zc, double* __restrict__ partials, int64_t nblk)
+k_prefilter(const float* __restrict__ f, int Z, int Y, int X, float a, float* __restrict__ g32,
+            double2* __restrict__ zc, double* __restrict__ partials)
 {
-    __shared__ double s1[kPreThreads], s2[kPreThreads];
+    __shared__ float warp_sums[kPreThreads / 32];
     const int64_t V = (int64_t)Z * Y * X;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double g = 0.0;
+    float g = 0.f;
     if (v < V) {
-        int x = (int)(v % X);
-        int64_t t = v / X;
-        int y = (int)(t % Y);
-        int z = (int)(t / Y);
-        const double tap[3] = {a, 1.0 - 2.0 * a, a};
+        const int x = (int)(v % X);
+        const int64_t t = v / X;
+        const int y = (int)(t % Y);
+        const int z = (int)(t / Y);
+        const float tap[3] = {a, 1.f - 2.f * a, a};
+#pragma unroll
         for (int dz = -1; dz <= 1; dz++) {
-            int zz = z + dz;
+            const int zz = z + dz;
             if (zz < 0 || zz >= Z) continue;
+#pragma unroll
             for (int dy = -1; dy <= 1; dy++) {
-                int yy = y + dy;
+                const int yy = y + dy;
                 if (yy < 0 || yy >= Y) continue;
                 const float* row = f + ((int64_t)zz * Y + yy) * X;
-                double ty = tap[dz + 1] * tap[dy + 1];
-                for (int dx = -1; dx <= 1; dx++) {
-                    int xx = x + dx;
-                    if (xx < 0 || xx >= X) continue;
-                    g += ty * tap[dx + 1] * (double)row[xx];
-                }
+                float r = tap[1] * __ldg(row + x);
+                if (x > 0) r += tap[0] * __ldg(row + x - 1);
+                if (x + 1 < X) r += tap[2] * __ldg(row + x + 1);
+                g += tap[dz + 1] * tap[dy + 1] * r;
             }
         }
-        g32[v] = (float)g;
-        zc[v] = make_double2(g, g * g);
+        g32[v] = g;
+        const double gd = (double)g;
+        zc[v] = make_double2(gd, gd * gd);
     }
-    s1[threadIdx.x] = v < V ? g : 0.0;
-    s2[threadIdx.x] = v < V ? g * g : 0.0;
+    float sq = g * g;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = sq;
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            s1[threadIdx.x] += s1[threadIdx.x + h];
-            s2[threadIdx.x] += s2[threadIdx.x + h];
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = s1[0];
-        partials[nblk + blockIdx.x] = s2[0];
+        double b = 0.0;
+        for (int i = 0; i < kPreThreads / 32; i++) b += warp_sums[i];
+        partials[blockIdx.x] = b;
     }
 }
 
-// floor = 1e-12 * M * var(g), fixed summation order
+// floor = 1e-12 * M * mean(g^2) (fixed summation order)
 __global__ void __launch_bounds__(1024)
 k_var_floor(const double* __restrict__ partials, int64_t nblk, int64_t V, double M, double* floor_out)
 {
-    __shared__ double s1[1024], s2[1024];
-    double a = 0, b = 0;
-    for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) {
-        a += partials[i];
-        b += partials[nblk + i];
-    }
-    s1[threadIdx.x] = a;
+    __shared__ double s2[1024];
+    double b = 0;
+    for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) b += partials[i];
     s2[threadIdx.x] = b;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            s1[threadIdx.x] += s1[threadIdx.x + h];
-            s2[threadIdx.x] += s2[threadIdx.x + h];
-        }
+        if (threadIdx.x < h) s2[threadIdx.x] += s2[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        double mean = s1[0] / (double)V;
-        double var = s2[0] / (double)V - mean * mean;
-        floor_out[0] = 1e-12 * M * var;
-    }
+    if (threadIdx.x == 0) floor_out[0] = 1e-12 * M * (s2[0] / (double)V);
 }
 
 // mask placed at the origin of the Z x Y x X grid (wrapped), as real rows
@@ -190,7 +180,9 @@ struct StoreW {
     {
         double S1 = v.x, S2 = v.y;
         double var = S2 - S1 * S1 / M;
-        w[l * X + j] = var > floor[0] ? (float)(1.0 / sqrt(var)) : 0.0f;
+        // zero local variance: below the volume-energy floor, or constant to
+        // ~5 digits over the window (the FFT leaves rounding noise there)
+        w[l * X + j] = (var > floor[0] && var > 1e-10 * S2) ? (float)(1.0 / sqrt(var)) : 0.0f;
     }
 };
 
@@ -216,7 +208,7 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
     p.G.alloc(Vh * sizeof(float2));
     p.zc.alloc(V * sizeof(double2));
     p.w.alloc(V * sizeof(float));
-    p.partials.alloc(2 * p.nblk_pre * sizeof(double));
+    p.partials.alloc(p.nblk_pre * sizeof(double));
     p.floor.alloc(sizeof(double));
     const int64_t noct = (int64_t)(Z / 2 + 1) * (Y / 2 + 1) * (X / 2 + 1);
     p.mhat.alloc(noct * sizeof(double));
@@ -232,10 +224,10 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
     cudaStream_t st = 0;
     double2* spec = p.zc.as<double2>();
     SrcWrappedMask src{p.mask_t.as<double>(), Y, X, Z, tz, ty, tx};
-    launch_r2c_rows<double>(src, (int64_t)Z * Y, spec, p.px64, st);
-    launch_strided<double, -1>(spec, StridedAxis{p.Xh, Z, (int64_t)Y * p.Xh, p.Xh}, p.py64,
+    launch_r2c_any<double>(src, (int64_t)Z * Y, spec, p.px64, st);
+    launch_strided_any<double, -1>(spec, StridedAxis{p.Xh, Z, (int64_t)Y * p.Xh, p.Xh}, p.py64,
                                ProIdentity<double>(), StoreTo<double>{spec, (int64_t)Y * p.Xh, p.Xh}, st);
-    launch_strided<double, -1>(spec, StridedAxis{(int64_t)Y * p.Xh, 1, 0, (int64_t)Y * p.Xh}, p.pz64,
+    launch_strided_any<double, -1>(spec, StridedAxis{(int64_t)Y * p.Xh, 1, 0, (int64_t)Y * p.Xh}, p.pz64,
                                ProIdentity<double>(), StoreTo<double>{spec, 0, (int64_t)Y * p.Xh}, st);
     k_mhat_octant<<<1024, 256, 0, st>>>(spec, Z, Y, p.Xh, X, 1.0 / (double)V, p.mhat.as<double>());
     TTM_LAUNCH_CHECK();
@@ -245,9 +237,9 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
 void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st)
 {
     const int64_t V = (int64_t)p.Z * p.Y * p.X;
-    k_prefilter<<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, p.filter_a, p.g32.as<float>(),
-                                                           p.zc.as<double2>(), p.partials.as<double>(),
-                                                           p.nblk_pre);
+    k_prefilter<<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
+                                                           p.g32.as<float>(), p.zc.as<double2>(),
+                                                           p.partials.as<double>());
     TTM_LAUNCH_CHECK();
     k_var_floor<<<1, 1024, 0, st>>>(p.partials.as<double>(), p.nblk_pre, V, p.M, p.floor.as<double>());
     TTM_LAUNCH_CHECK();
@@ -258,10 +250,10 @@ void prep_spectrum(Prep& p, cudaStream_t st)
 {
     const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
     float2* G = p.G.as<float2>();
-    launch_r2c_rows<float>(SrcFloat{p.g32.as<float>(), X}, (int64_t)Z * Y, G, p.px32, st);
-    launch_strided<float, -1>(G, StridedAxis{Xh, Z, (int64_t)Y * Xh, Xh}, p.py32, ProIdentity<float>(),
+    launch_r2c_any<float>(SrcFloat{p.g32.as<float>(), X}, (int64_t)Z * Y, G, p.px32, st);
+    launch_strided_any<float, -1>(G, StridedAxis{Xh, Z, (int64_t)Y * Xh, Xh}, p.py32, ProIdentity<float>(),
                               StoreTo<float>{G, (int64_t)Y * Xh, Xh}, st);
-    launch_strided<float, -1>(G, StridedAxis{(int64_t)Y * Xh, 1, 0, (int64_t)Y * Xh}, p.pz32,
+    launch_strided_any<float, -1>(G, StridedAxis{(int64_t)Y * Xh, 1, 0, (int64_t)Y * Xh}, p.pz32,
                               ProIdentity<float>(), StoreTo<float>{G, 0, (int64_t)Y * Xh}, st);
 }
 
@@ -272,16 +264,16 @@ void prep_localsums(Prep& p, cudaStream_t st)
     const int Z = p.Z, Y = p.Y, X = p.X;
     double2* zc = p.zc.as<double2>();
     const int64_t YX = (int64_t)Y * X;
-    launch_contig<double, -1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(), StoreTo<double>{zc, X, 1}, st);
-    launch_strided<double, -1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
+    launch_contig_any<double, -1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(), StoreTo<double>{zc, X, 1}, st);
+    launch_strided_any<double, -1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
                                StoreTo<double>{zc, YX, X}, st);
-    launch_strided<double, -1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64, ProIdentity<double>(),
+    launch_strided_any<double, -1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64, ProIdentity<double>(),
                                StoreTo<double>{zc, 0, YX}, st);
-    launch_strided<double, +1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64,
+    launch_strided_any<double, +1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64,
                                ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, StoreTo<double>{zc, 0, YX}, st);
-    launch_strided<double, +1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
+    launch_strided_any<double, +1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
                                StoreTo<double>{zc, YX, X}, st);
-    launch_contig<double, +1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(),
+    launch_contig_any<double, +1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(),
                               StoreW{p.w.as<float>(), p.floor.as<double>(), p.M, X}, st);
 }
 

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -123,13 +124,13 @@ extern "C" ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int
                     2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
             k_rotate_template<<<64, 256, 0, st>>>(tp.as<double>(), tz, ty, tx, R, 1.0 / (double)V, rot.as<float>());
             TTM_LAUNCH_CHECK();
-            launch_r2c_rows<float>(SrcTemplateRows{rot.as<float>(), Y, X, ty, tx}, (int64_t)tz * Y, pt, p.px32, st);
-            launch_strided<float, -1>(pt, StridedAxis{Xh, tz, ncols, Xh}, p.py32, ProIdentity<float>(),
+            launch_r2c_any<float>(SrcTemplateRows{rot.as<float>(), Y, X, ty, tx}, (int64_t)tz * Y, pt, p.px32, st);
+            launch_strided_any<float, -1>(pt, StridedAxis{Xh, tz, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{pt, ncols, Xh}, st);
             launch_zcorr(p.G.as<float2>(), pt, 1, tz, tz / 2, ncols, wk, p.pz32, st);
-            launch_strided<float, +1>(wk, StridedAxis{Xh, Z, ncols, Xh}, p.py32, ProIdentity<float>(),
+            launch_strided_any<float, +1>(wk, StridedAxis{Xh, Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{wk, ncols, Xh}, st);
-            launch_c2r_rows<float>(wk, (int64_t)Z * Y, SinkTMMax{p.w.as<float>(), d_best, d_best_idx, X, (int32_t)j},
+            launch_c2r_any<float>(wk, (int64_t)Z * Y, SinkTMMax{p.w.as<float>(), d_best, d_best_idx, X, (int32_t)j},
                                    p.px32, 1, st);
         }
         TTM_CUDA_TRY(cudaStreamSynchronize(st));
