@@ -188,6 +188,7 @@ def run_ours(args, ws, rank, local):
     m = ttm.Matcher(ctx, wl.template, p, (Z, Y, X), device=dev)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    ttm.ttm_plan_set_localsum(m.plan, ttm.TTM_LOCALSUM_DF64 if args.localsum == "df64" else ttm.TTM_LOCALSUM_FP64)
     d_tomo = torch.as_tensor(wl.tomo, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -275,7 +276,8 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": WORKLOAD, "shape_zyx": [Z, Y, X], "template": 40, "order_n": n,
                            "components": K, "mask_radius": wl.mask_radius, "rotations_field": 24 * 2048,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1gpu",
-                           "local_sums": "fp64", "spectra": "fp32"},
+                           "local_sums": {"df64": "double-float (FP32 pairs, ~48-bit significand)",
+                                          "fp64": "fp64"}[args.localsum], "spectra": "fp32"},
                 "roofline": roof, "stages_ms": st_ms, "setup_s": setup_s,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": V * 4,
@@ -292,6 +294,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-voxels", type=int, default=60000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--localsum", default="df64", choices=["df64", "fp64"],
+                    help="arithmetic of the local sums of Eq. 2")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

@@ -145,6 +145,15 @@ void ttm_plan_valid_box(const ttm_plan* plan, int* box6);
  *   d_C     float32 [K][Z][Y][X] output (device) */
 ttm_status ttm_correlate(ttm_plan* plan, const float* d_tomo, float* d_C, void* stream);
 
+/* Arithmetic of the local sums S1, S2 and of the variance of Eq. 2:
+ *   TTM_LOCALSUM_FP64 (default): FP64 transforms and FP64 variance;
+ *   TTM_LOCALSUM_DF64: double-float arithmetic (each value an unevaluated
+ *   sum of two FP32 numbers, ~48-bit significand, FP32 exponent range) on the
+ *   FP32 pipes, variance formed in double-float.
+ * Takes effect at the next ttm_correlate. */
+typedef enum { TTM_LOCALSUM_FP64 = 0, TTM_LOCALSUM_DF64 = 1 } ttm_localsum_precision;
+ttm_status ttm_plan_set_localsum(ttm_plan* plan, int mode);
+
 /* Local normaliser w of the last ttm_correlate on this plan, float32
  * [Z][Y][X] copied to d_w (device). */
 ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream);

@@ -48,10 +48,10 @@ TwiddleCache::~TwiddleCache()
     std::free(entries_);
 }
 
-const void* TwiddleCache::get(int L, bool dbl)
+const void* TwiddleCache::get(int L, int kind)
 {
     for (int i = 0; i < n_; i++)
-        if (entries_[i].L == L && entries_[i].dbl == dbl) return entries_[i].ptr;
+        if (entries_[i].L == L && entries_[i].kind == kind) return entries_[i].ptr;
     // exp(-2 pi i m / L) from the exact fraction m / L, in double precision
     std::vector<double> re(L), im(L);
     for (int m = 0; m < L; m++) {
@@ -60,11 +60,20 @@ const void* TwiddleCache::get(int L, bool dbl)
         im[m] = -std::sin(a);
     }
     void* d = nullptr;
-    size_t bytes = (size_t)L * (dbl ? sizeof(double2) : sizeof(float2));
+    const size_t esz = kind == TW_F32 ? sizeof(float2) : sizeof(double2);
+    const size_t bytes = (size_t)L * esz;
     TTM_CUDA_TRY(cudaMalloc(&d, bytes));
-    if (dbl) {
+    if (kind == TW_F64) {
         std::vector<double2> h(L);
         for (int m = 0; m < L; m++) h[m] = make_double2(re[m], im[m]);
+        TTM_CUDA_TRY(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
+    } else if (kind == TW_DF64) {
+        // (re.hi, re.lo, im.hi, im.lo)
+        std::vector<float4> h(L);
+        for (int m = 0; m < L; m++) {
+            float rh = (float)re[m], ih = (float)im[m];
+            h[m] = make_float4(rh, (float)(re[m] - (double)rh), ih, (float)(im[m] - (double)ih));
+        }
         TTM_CUDA_TRY(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
     } else {
         std::vector<float2> h(L);
@@ -75,16 +84,16 @@ const void* TwiddleCache::get(int L, bool dbl)
         cap_ = cap_ ? 2 * cap_ : 8;
         entries_ = (Entry*)std::realloc(entries_, sizeof(Entry) * cap_);
     }
-    entries_[n_++] = Entry{L, dbl, d};
+    entries_[n_++] = Entry{L, kind, d};
     return d;
 }
 
-LenPlan make_len_plan(TwiddleCache& tc, int L, bool dbl)
+LenPlan make_len_plan(TwiddleCache& tc, int L, int kind)
 {
     LenPlan pl;
     TTM_REQUIRE(factor_length(L, pl), E_SHAPE,
                 "transform length " + std::to_string(L) + " is not a product of 2, 3, 5 and 7");
-    pl.tw = tc.get(L, dbl);
+    pl.tw = tc.get(L, kind);
     return pl;
 }
 

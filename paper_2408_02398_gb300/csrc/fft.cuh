@@ -15,6 +15,7 @@
 #pragma once
 
 #include "ttm_common.cuh"
+#include "df64.cuh"
 
 namespace ttm {
 
@@ -382,19 +383,22 @@ TileShape choose_tile(int L, size_t elem_bytes, int min_w, int max_w);
 namespace ttm {
 
 // Device twiddle tables, one per (length, precision), owned by a context.
+// twiddle precision: FP32, FP64, or double-float pairs
+enum TwKind { TW_F32 = 0, TW_F64 = 1, TW_DF64 = 2 };
+
 class TwiddleCache {
   public:
     ~TwiddleCache();
-    const void* get(int L, bool dbl);
+    const void* get(int L, int kind);
 
   private:
-    struct Entry { int L; bool dbl; void* ptr; };
+    struct Entry { int L; int kind; void* ptr; };
     Entry* entries_ = nullptr;
     int n_ = 0, cap_ = 0;
 };
 
-// LenPlan for L with the twiddles of the given precision.
-LenPlan make_len_plan(TwiddleCache& tc, int L, bool dbl);
+// LenPlan for L with the twiddles of the given precision (TwKind).
+LenPlan make_len_plan(TwiddleCache& tc, int L, int kind);
 
 template <typename K>
 inline void set_smem(K kernel, size_t bytes)

@@ -74,6 +74,7 @@ __device__ __forceinline__ void dft_reg(cx<R>* v, const cx<R>* __restrict__ tw)
 // thread counts and shared-memory layout of a four-step tile of W lines
 template <typename R> struct FsThreads { static constexpr int value = 256; };
 template <> struct FsThreads<double> { static constexpr int value = 128; };
+template <> struct FsThreads<df64> { static constexpr int value = 128; };
 
 template <typename R, int E, int P> struct FsShape {
     static constexpr int L = E * P;

@@ -7,7 +7,7 @@
 
 namespace ttm {
 
-void upload_probe_tables();
+void upload_probe_tables(ttm_ctx* ctx);
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -80,7 +80,7 @@ extern "C" ttm_status ttm_ctx_create(int device, ttm_ctx** out)
     try {
         TTM_CUDA_TRY(cudaSetDevice(device));
         TTM_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
-        upload_probe_tables();
+        upload_probe_tables(c);
         *out = c;
         return TTM_OK;
     } catch (const Error& e) {

@@ -101,7 +101,9 @@ struct SinkNormalise {
     __device__ void operator()(int batch, int64_t row, int x, float v) const
     {
         int64_t i = row * X + x;
-        C[(int64_t)batch * V + i] = w[i] * v;
+        // w is read-only for the whole pass: the read-only path lets these
+        // loads be issued ahead of the stores to C
+        C[(int64_t)batch * V + i] = __ldg(w + i) * v;
     }
 };
 
@@ -261,4 +263,11 @@ extern "C" ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream)
     } catch (const Error& e) {
         return (ttm_status)fail(plan->ctx, e);
     }
+}
+
+extern "C" ttm_status ttm_plan_set_localsum(ttm_plan* plan, int mode)
+{
+    if (!plan || (mode != TTM_LOCALSUM_FP64 && mode != TTM_LOCALSUM_DF64)) return TTM_E_INVALID_ARG;
+    plan->prep.localsum_mode = mode;
+    return TTM_OK;
 }

@@ -40,7 +40,9 @@ struct Prep {
     DevBuf partials;           // double [2][nblk_pre]
     DevBuf floor;              // double [1]: variance floor
     DevBuf mask_t;             // double [tz][ty][tx] mask on the template grid
-    LenPlan px32, py32, pz32, px64, py64, pz64;
+    DevBuf mhat_df;            // float2 (hi, lo) copy of mhat for the double-float sums
+    int localsum_mode = 0;     // 0: FP64, 1: double-float (FP32 pairs)
+    LenPlan px32, py32, pz32, px64, py64, pz64, pxd, pyd, pzd;
 };
 
 void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
@@ -66,6 +68,8 @@ struct ttm_ctx {
     std::string last_error;
     ttm::TwiddleCache twiddles;
     int num_sms = 0;
+    ttm::DevBuf probe_tables;  // maximiser probe directions and monomials
+    size_t probe_off[5] = {0, 0, 0, 0, 0};
 };
 
 struct ttm_plan {

@@ -3,43 +3,47 @@
 //   F(x) = ||C(x)||_F,  s(x) = max_{|u|=1} p_x(u),  u*(x) = argmax,
 //   p_x(u) = C(x) . u^{(x)n} = sum_alpha mult(alpha) C_alpha(x) u^alpha.
 //
-// One thread per voxel, components loaded structure-of-arrays (coalesced).
-// The form is evaluated at P fixed probe directions on the half-sphere
-// (p is even); the probes whose value is not below any of their nearest
-// probes (discrete local maxima) are the candidate basins, and the best NS
-// of them are polished on the sphere. The derivatives come from the
-// contraction A = C . u^{n-2} (a symmetric 3x3 matrix): p = u^T A u,
-// grad p = n A u, Hess p = n (n-1) A. Each polish step is a Riemannian
-// Newton step in a Householder tangent basis, limited to 0.5 rad; where the
-// tangent Hessian is not negative definite it is shifted until it is (a
-// Levenberg-Marquardt step), the step is halved until p does not decrease,
-// and a shifted power step (SS-HOPM, shift (n-1)||C||_F, never decreasing)
-// is the last resort.
+// One thread per voxel, components loaded structure-of-arrays (coalesced),
+// persistent CTAs. The form is evaluated at P fixed probe directions on the
+// half-sphere (p is even; the probe table sits in shared memory and is read
+// as broadcast float4s; probe values are kept in FP16, only to pick starts).
+// The probes that are not below any of their nearest probes (discrete local
+// maxima) and lie within 0.2 ||C||_F of the best probe are the candidate
+// basins; the best NS of them (2, 3, 4 for n = 2, 4, 6) get two interleaved
+// Newton steps each and the best of those is polished to convergence. The
+// derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
+// matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
+// is a Riemannian Newton step in a Householder tangent basis, limited to
+// 0.5 rad; where the tangent Hessian is not negative definite it is shifted
+// until it is (a Levenberg-Marquardt step), the step is halved until p does
+// not decrease, and a shifted power step (SS-HOPM, shift (n-1)||C||_F, never
+// decreasing) is the last resort.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "ttm_internal.h"
 
 namespace ttm {
 
 constexpr int kProbes = 128;
-constexpr int kProbeNbr = 6;
 constexpr int kPmThreads = 128;
-constexpr int kStarts = 4;
-constexpr int kNewtonIters = 12;
-
-__constant__ float c_phi2[kProbes * 6];
-__constant__ float c_phi4[kProbes * 15];
-__constant__ float c_phi6[kProbes * 28];
-__constant__ float c_dir[kProbes * 3];
-__constant__ unsigned char c_nbr[kProbes * kProbeNbr];
-
-template <int N> __device__ __forceinline__ const float* phi_table();
-template <> __device__ __forceinline__ const float* phi_table<2>() { return c_phi2; }
-template <> __device__ __forceinline__ const float* phi_table<4>() { return c_phi4; }
-template <> __device__ __forceinline__ const float* phi_table<6>() { return c_phi6; }
+constexpr int kPreIters = 2;      // cheap polish of every start
+constexpr int kNewtonIters = 10;  // full polish of the best one
+constexpr int kProbeNbr = 6;
+// probes more than this fraction of ||C||_F below the best probe are not
+// considered as starts
+constexpr float kStartMargin = 0.2f;
 
 __host__ __device__ constexpr int ncomp3(int n) { return (n + 1) * (n + 2) / 2; }
+// starts polished per voxel: order 2 has a single maximum pair; higher
+// orders have more, narrower maxima (and the FP16 probe values can reorder
+// near-equal candidates)
+__host__ __device__ constexpr int nstarts(int n) { return n >= 6 ? 4 : (n >= 4 ? 3 : 2); }
+__host__ __device__ constexpr int kpad(int n) { return (ncomp3(n) + 3) / 4 * 4; }
 __host__ __device__ constexpr float factf(int n) { return n <= 1 ? 1.f : n * factf(n - 1); }
 // position of exponents (a, b, n-a-b) in graded-lex descending order
 __host__ __device__ constexpr int cidx(int n, int a, int b) { return (n - a) * (n - a + 1) / 2 + (n - a - b); }
@@ -72,15 +76,13 @@ __device__ __forceinline__ void contract2(const float* c, float ux, float uy, fl
     }
 }
 
+// p = u^T A u at u, with A = C . u^{N-2} (also returned)
 template <int N>
-__device__ __forceinline__ float form_value(const float* c, float ux, float uy, float uz)
+__device__ __forceinline__ float form_at(const float* c, float ux, float uy, float uz, float* A)
 {
-    float A[6];
     contract2<N>(c, ux, uy, uz, A);
-    float ax = A[0] * ux + A[1] * uy + A[2] * uz;
-    float ay = A[1] * ux + A[3] * uy + A[4] * uz;
-    float az = A[2] * ux + A[4] * uy + A[5] * uz;
-    return ux * ax + uy * ay + uz * az;
+    return ux * (A[0] * ux + A[1] * uy + A[2] * uz) + uy * (A[1] * ux + A[3] * uy + A[4] * uz) +
+           uz * (A[2] * ux + A[4] * uy + A[5] * uz);
 }
 
 __device__ __forceinline__ void normalise3(float& x, float& y, float& z)
@@ -89,21 +91,19 @@ __device__ __forceinline__ void normalise3(float& x, float& y, float& z)
     x *= s; y *= s; z *= s;
 }
 
-// polish u to a local maximum of p; returns p(u)
-template <int N>
-__device__ float polish(const float* c, float frob, float& ux, float& uy, float& uz)
+// up to ITERS polish steps of u towards a local maximum of p; p and A hold
+// the value and contraction at u on entry and on return
+template <int N, int ITERS>
+__device__ void polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p, float* A)
 {
     const float tol_g2 = 1e-12f * frob * frob;  // |tangent gradient| <= 1e-6 ||C||_F
     const float tol_p = 1e-7f * frob;
     const float hN = (float)(N * (N - 1));
-    float p = 0.f;
-    for (int it = 0; it < kNewtonIters; it++) {
-        float A[6];
-        contract2<N>(c, ux, uy, uz, A);
+#pragma unroll 1
+    for (int it = 0; it < ITERS; it++) {
         const float ax = A[0] * ux + A[1] * uy + A[2] * uz;
         const float ay = A[1] * ux + A[3] * uy + A[4] * uz;
         const float az = A[2] * ux + A[4] * uy + A[5] * uz;
-        p = ux * ax + uy * ay + uz * az;
         // grad = N A u, Hess = N (N-1) A, u . grad = N p.
         // Tangent basis: the Householder reflection of v = u + sign(u_k) e_k
         // (k = largest |u_k|) maps e_k to -+u; its other two columns
@@ -125,7 +125,6 @@ __device__ float polish(const float* c, float frob, float& ux, float& uy, float&
         const float g0 = N * (b0x * ax + b0y * ay + b0z * az);
         const float g1 = N * (b1x * ax + b1y * ay + b1z * az);
         if (g0 * g0 + g1 * g1 <= tol_g2) break;
-        // A b0, A b1
         const float a0x = A[0] * b0x + A[1] * b0y + A[2] * b0z;
         const float a0y = A[1] * b0x + A[3] * b0y + A[4] * b0z;
         const float a0z = A[2] * b0x + A[4] * b0y + A[5] * b0z;
@@ -149,11 +148,17 @@ __device__ float polish(const float* c, float frob, float& ux, float& uy, float&
         bool moved = false;
         float t = 1.f;
 #pragma unroll 1
-        for (int bt = 0; bt < 4; bt++, t *= 0.5f) {
+        for (int bt = 0; bt < 4 && !moved; bt++, t *= 0.5f) {
             float nx = ux + t * dx, ny = uy + t * dy, nz = uz + t * dz;
             normalise3(nx, ny, nz);
-            const float pn = form_value<N>(c, nx, ny, nz);
-            if (pn >= p - tol_p) { ux = nx; uy = ny; uz = nz; p = pn; moved = true; break; }
+            float An[6];
+            const float pn = form_at<N>(c, nx, ny, nz, An);
+            if (pn >= p - tol_p) {
+                ux = nx; uy = ny; uz = nz; p = pn;
+#pragma unroll
+                for (int i = 0; i < 6; i++) A[i] = An[i];
+                moved = true;
+            }
         }
         if (!moved) {
             // shifted power step: u <- normalise(A u + (N-1) ||C||_F u), never decreases p
@@ -161,95 +166,234 @@ __device__ float polish(const float* c, float frob, float& ux, float& uy, float&
             float nx = ax + shift * ux, ny = ay + shift * uy, nz = az + shift * uz;
             normalise3(nx, ny, nz);
             ux = nx; uy = ny; uz = nz;
+            p = form_at<N>(c, ux, uy, uz, A);
         }
     }
-    return form_value<N>(c, ux, uy, uz);
 }
+
+// One Newton step (as in polish) for NS starts at once: the starts are
+// independent, so their dependency chains interleave. A step is tried at
+// full and half length; if neither keeps p, a shifted power step is taken.
+template <int N, int NS>
+__device__ __forceinline__ void newton_step_multi(const float* c, float frob, float (*u)[3], float* p, float (*A)[6],
+                                                  const bool* live)
+{
+    const float tol_p = 1e-7f * frob;
+    const float hN = (float)(N * (N - 1));
+    float d[NS][3];
+    bool moved[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const float ux = u[s][0], uy = u[s][1], uz = u[s][2];
+        const float* a = A[s];
+        const float ax = a[0] * ux + a[1] * uy + a[2] * uz;
+        const float ay = a[1] * ux + a[3] * uy + a[4] * uz;
+        const float az = a[2] * ux + a[4] * uy + a[5] * uz;
+        const float fx = fabsf(ux), fy = fabsf(uy), fz = fabsf(uz);
+        const int kmax = (fx >= fy && fx >= fz) ? 0 : (fy >= fz ? 1 : 2);
+        const float vx = ux + (kmax == 0 ? (ux >= 0.f ? 1.f : -1.f) : 0.f);
+        const float vy = uy + (kmax == 1 ? (uy >= 0.f ? 1.f : -1.f) : 0.f);
+        const float vz = uz + (kmax == 2 ? (uz >= 0.f ? 1.f : -1.f) : 0.f);
+        const float r2 = __fdividef(2.f, vx * vx + vy * vy + vz * vz);
+        const float vj1 = kmax == 0 ? vy : vx, vj2 = kmax == 2 ? vy : vz;
+        const float b0x = (kmax != 0 ? 1.f : 0.f) - r2 * vj1 * vx, b0y = (kmax == 0 ? 1.f : 0.f) - r2 * vj1 * vy,
+                    b0z = -r2 * vj1 * vz;
+        const float b1x = -r2 * vj2 * vx, b1y = (kmax == 2 ? 1.f : 0.f) - r2 * vj2 * vy,
+                    b1z = (kmax != 2 ? 1.f : 0.f) - r2 * vj2 * vz;
+        const float g0 = N * (b0x * ax + b0y * ay + b0z * az);
+        const float g1 = N * (b1x * ax + b1y * ay + b1z * az);
+        const float a0x = a[0] * b0x + a[1] * b0y + a[2] * b0z, a0y = a[1] * b0x + a[3] * b0y + a[4] * b0z,
+                    a0z = a[2] * b0x + a[4] * b0y + a[5] * b0z;
+        const float a1x = a[0] * b1x + a[1] * b1y + a[2] * b1z, a1y = a[1] * b1x + a[3] * b1y + a[4] * b1z,
+                    a1z = a[2] * b1x + a[4] * b1y + a[5] * b1z;
+        float h00 = N * p[s] - hN * (b0x * a0x + b0y * a0y + b0z * a0z);
+        const float h01 = -hN * (b1x * a0x + b1y * a0y + b1z * a0z);
+        float h11 = N * p[s] - hN * (b1x * a1x + b1y * a1y + b1z * a1z);
+        const float mid = 0.5f * (h00 + h11), dif = 0.5f * (h00 - h11);
+        const float lmin = mid - sqrtf(dif * dif + h01 * h01);
+        if (lmin <= 1e-6f * frob) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
+        const float idet = __frcp_rn(h00 * h11 - h01 * h01);
+        float x0 = (h11 * g0 - h01 * g1) * idet, x1 = (h00 * g1 - h01 * g0) * idet;
+        const float xn2 = x0 * x0 + x1 * x1;
+        if (xn2 > 0.25f) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
+        d[s][0] = x0 * b0x + x1 * b1x;
+        d[s][1] = x0 * b0y + x1 * b1y;
+        d[s][2] = x0 * b0z + x1 * b1z;
+        moved[s] = !live[s];
+    }
+#pragma unroll
+    for (int bt = 0; bt < 2; bt++) {
+        const float t = bt == 0 ? 1.f : 0.5f;
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            float nx = u[s][0] + t * d[s][0], ny = u[s][1] + t * d[s][1], nz = u[s][2] + t * d[s][2];
+            normalise3(nx, ny, nz);
+            float An[6];
+            const float pn = form_at<N>(c, nx, ny, nz, An);
+            if (!moved[s] && pn >= p[s] - tol_p) {
+                u[s][0] = nx; u[s][1] = ny; u[s][2] = nz; p[s] = pn;
+#pragma unroll
+                for (int i = 0; i < 6; i++) A[s][i] = An[i];
+                moved[s] = true;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (moved[s]) continue;
+        const float shift = (N - 1) * frob;
+        const float* a = A[s];
+        float nx = a[0] * u[s][0] + a[1] * u[s][1] + a[2] * u[s][2] + shift * u[s][0];
+        float ny = a[1] * u[s][0] + a[3] * u[s][1] + a[4] * u[s][2] + shift * u[s][1];
+        float nz = a[2] * u[s][0] + a[4] * u[s][1] + a[5] * u[s][2] + shift * u[s][2];
+        normalise3(nx, ny, nz);
+        u[s][0] = nx; u[s][1] = ny; u[s][2] = nz;
+        p[s] = form_at<N>(c, nx, ny, nz, A[s]);
+    }
+}
+
+// probe tables: directions [kProbes][4] (x, y, z, 0) and weighted monomials
+// [kProbes][kpad(n)] for n = 2, 4, 6, in global memory
+struct ProbeTables {
+    const float4* dir;
+    const float* phi2;
+    const float* phi4;
+    const float* phi6;
+    const unsigned char* nbr;  // [kProbes][kProbeNbr] nearest probes (u ~ -u)
+};
 
 template <int N>
 __global__ void __launch_bounds__(kPmThreads)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
-          float* __restrict__ frob)
+          float* __restrict__ frob, ProbeTables tabs)
 {
     constexpr int K = ncomp3(N);
-    extern __shared__ float pv[];  // [kProbes][kPmThreads]
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ok = v < V;
-    float c[K];
-    float F2 = 0.f;
+    constexpr int KP = kpad(N);
+    constexpr int kStarts = nstarts(N);
+    __shared__ float4 sdir[kProbes];
+    __shared__ __align__(16) float sphi[kProbes * KP];
+    __shared__ unsigned char snbr[kProbes * kProbeNbr];
+    // [kProbes][kPmThreads] probe values, FP16 (only used to pick starts)
+    extern __shared__ __half pv[];
     {
-        int k = 0;
+        const float* phi = N == 2 ? tabs.phi2 : (N == 4 ? tabs.phi4 : tabs.phi6);
+        for (int i = threadIdx.x; i < kProbes * KP; i += blockDim.x) sphi[i] = phi[i];
+        for (int i = threadIdx.x; i < kProbes; i += blockDim.x) sdir[i] = tabs.dir[i];
+        for (int i = threadIdx.x; i < kProbes * kProbeNbr; i += blockDim.x) snbr[i] = tabs.nbr[i];
+    }
+    __syncthreads();
+    // persistent: each CTA walks voxel blocks with a grid stride
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - threadIdx.x < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = v < V;
+        float c[KP];
+        float F2 = 0.f;
+        {
+            int k = 0;
 #pragma unroll
-        for (int a = N; a >= 0; a--)
+            for (int a = N; a >= 0; a--)
 #pragma unroll
-            for (int b = N - a; b >= 0; b--) {
-                const int cc = N - a - b;
-                const float mult = factf(N) / (factf(a) * factf(b) * factf(cc));
-                c[k] = ok ? C[(int64_t)k * V + v] : 0.f;
-                F2 += mult * c[k] * c[k];
-                k++;
+                for (int b = N - a; b >= 0; b--) {
+                    const int cc = N - a - b;
+                    const float mult = factf(N) / (factf(a) * factf(b) * factf(cc));
+                    c[k] = ok ? __ldg(C + (int64_t)k * V + v) : 0.f;
+                    F2 += mult * c[k] * c[k];
+                    k++;
+                }
+#pragma unroll
+            for (int k2 = K; k2 < KP; k2++) c[k2] = 0.f;
+        }
+        const float F = sqrtf(F2);
+        // probe values to shared memory (one column per thread), and their max
+        float pmax = -INFINITY;
+#pragma unroll 2
+        for (int j = 0; j < kProbes; j++) {
+            const float4* ph = reinterpret_cast<const float4*>(sphi + j * KP);
+            float pj = 0.f;
+#pragma unroll
+            for (int q = 0; q < KP / 4; q++) {
+                const float4 f = ph[q];
+                pj += f.x * c[4 * q] + f.y * c[4 * q + 1] + f.z * c[4 * q + 2] + f.w * c[4 * q + 3];
             }
-    }
-    const float F = sqrtf(F2);
-    const float* phi = phi_table<N>();
-#pragma unroll 4
-    for (int j = 0; j < kProbes; j++) {
-        float acc = 0.f;
+            pv[j * kPmThreads + threadIdx.x] = __float2half_rn(pj);
+            pmax = fmaxf(pmax, pj);
+        }
+        // starts: the best kStarts discrete local maxima (not below any of
+        // their kProbeNbr nearest probes) within kStartMargin ||C||_F of the
+        // best probe, kept sorted in registers
+        const float thr = pmax - kStartMargin * F;
+        float sv[kStarts];
+        int sj[kStarts];
 #pragma unroll
-        for (int k = 0; k < K; k++) acc += phi[j * K + k] * c[k];
-        pv[j * kPmThreads + threadIdx.x] = acc;
-    }
-    // best kStarts discrete local maxima (value desc, probe index asc); a
-    // probe is examined only if it would enter the list (kept in registers:
-    // insertion by unrolled compare-and-swap)
-    int sj[kStarts];
-    float sv[kStarts];
+        for (int s = 0; s < kStarts; s++) { sv[s] = -INFINITY; sj[s] = 0; }
+        for (int j = 0; j < kProbes; j++) {
+            const float pj = __half2float(pv[j * kPmThreads + threadIdx.x]);
+            if (pj < thr || !(pj > sv[kStarts - 1])) continue;
+            bool is_max = true;
 #pragma unroll
-    for (int s = 0; s < kStarts; s++) { sj[s] = -1; sv[s] = -INFINITY; }
-    for (int j = 0; j < kProbes; j++) {
-        const float pj = pv[j * kPmThreads + threadIdx.x];
-        if (!(pj > sv[kStarts - 1])) continue;
-        bool is_max = true;
+            for (int b = 0; b < kProbeNbr; b++)
+                if (__half2float(pv[snbr[j * kProbeNbr + b] * kPmThreads + threadIdx.x]) > pj) is_max = false;
+            if (!is_max) continue;
+            float cv = pj;
+            int cj = j;
 #pragma unroll
-        for (int b = 0; b < kProbeNbr; b++)
-            if (pv[c_nbr[j * kProbeNbr + b] * kPmThreads + threadIdx.x] > pj) is_max = false;
-        if (!is_max) continue;
-        float cv = pj;
-        int cj = j;
-#pragma unroll
-        for (int s = 0; s < kStarts; s++) {
-            if (cv > sv[s]) {
-                const float tv = sv[s]; const int tj = sj[s];
-                sv[s] = cv; sj[s] = cj;
-                cv = tv; cj = tj;
+            for (int s = 0; s < kStarts; s++) {
+                if (cv > sv[s]) {
+                    const float tv = sv[s]; const int tj = sj[s];
+                    sv[s] = cv; sj[s] = cj;
+                    cv = tv; cj = tj;
+                }
             }
         }
-    }
-    float best = -INFINITY, bx = 0.f, by = 0.f, bz = 1.f;
+        // two interleaved Newton steps from every start, then the full
+        // polish of the best
+        float best = 0.f, bx = 0.f, by = 0.f, bz = 1.f;
+        if (F > 0.f) {
+            float u[kStarts][3], ps[kStarts], A[kStarts][6];
+            bool live[kStarts];
 #pragma unroll
-    for (int s = 0; s < kStarts; s++) {
-        if (sj[s] < 0 || F == 0.f) continue;
-        float ux = c_dir[3 * sj[s]], uy = c_dir[3 * sj[s] + 1], uz = c_dir[3 * sj[s] + 2];
-        const float ps = polish<N>(c, F, ux, uy, uz);
-        if (ps > best) { best = ps; bx = ux; by = uy; bz = uz; }
-    }
-    if (F == 0.f) best = 0.f;
-    // canonical half-sphere: last non-zero of (z, y, x) positive
-    if (bz < 0.f || (bz == 0.f && (by < 0.f || (by == 0.f && bx < 0.f)))) { bx = -bx; by = -by; bz = -bz; }
-    if (ok) {
-        score[v] = best;
-        orient[v] = bx;
-        orient[V + v] = by;
-        orient[2 * V + v] = bz;
-        if (frob) frob[v] = F;
+            for (int s = 0; s < kStarts; s++) {
+                live[s] = sv[s] > -INFINITY;
+                const float4 d = sdir[live[s] ? sj[s] : sj[0]];
+                u[s][0] = d.x; u[s][1] = d.y; u[s][2] = d.z;
+                ps[s] = form_at<N>(c, d.x, d.y, d.z, A[s]);
+            }
+#pragma unroll 1
+            for (int it = 0; it < kPreIters; it++) newton_step_multi<N, kStarts>(c, F, u, ps, A, live);
+            int bs = 0;
+#pragma unroll
+            for (int s = 1; s < kStarts; s++)
+                if (live[s] && ps[s] > ps[bs]) bs = s;
+            float bA[6];
+            best = ps[0]; bx = u[0][0]; by = u[0][1]; bz = u[0][2];
+#pragma unroll
+            for (int i = 0; i < 6; i++) bA[i] = A[0][i];
+#pragma unroll
+            for (int s = 1; s < kStarts; s++)
+                if (s == bs) {
+                    best = ps[s]; bx = u[s][0]; by = u[s][1]; bz = u[s][2];
+#pragma unroll
+                    for (int i = 0; i < 6; i++) bA[i] = A[s][i];
+                }
+            polish<N, kNewtonIters>(c, F, bx, by, bz, best, bA);
+        }
+        // canonical half-sphere: last non-zero of (z, y, x) positive
+        if (bz < 0.f || (bz == 0.f && (by < 0.f || (by == 0.f && bx < 0.f)))) { bx = -bx; by = -by; bz = -bz; }
+        if (ok) {
+            score[v] = best;
+            orient[v] = bx;
+            orient[V + v] = by;
+            orient[2 * V + v] = bz;
+            if (frob) frob[v] = F;
+        }
     }
 }
 
 // ---------------------------------------------------------------- host --
 
-// probe directions (spherical Fibonacci on the half-sphere z > 0), their
-// nearest neighbours (u ~ -u) and the weighted monomials per order
-void upload_probe_tables()
+// probe directions (spherical Fibonacci on the half-sphere z > 0) and the
+// multiplicity-weighted monomials of each order, padded to float4 rows
+void build_probe_tables(std::vector<float>& out, size_t off[5])
 {
     const double ga = M_PI * (3.0 - std::sqrt(5.0));
     std::vector<double> d(3 * kProbes);
@@ -259,50 +403,83 @@ void upload_probe_tables()
         d[3 * i + 1] = r * std::sin(ph);
         d[3 * i + 2] = z;
     }
+    out.clear();
+    off[0] = 0;
+    for (int i = 0; i < kProbes; i++) {
+        out.push_back((float)d[3 * i]); out.push_back((float)d[3 * i + 1]);
+        out.push_back((float)d[3 * i + 2]); out.push_back(0.f);
+    }
+    int slot = 1;
+    for (int n : {2, 4, 6}) {
+        off[slot++] = out.size();
+        const int K = ncomp3(n), KP = kpad(n);
+        for (int j = 0; j < kProbes; j++) {
+            int k = 0;
+            for (int a = n; a >= 0; a--)
+                for (int b = n - a; b >= 0; b--, k++) {
+                    int c = n - a - b;
+                    double mult = std::tgamma(n + 1.0) / (std::tgamma(a + 1.0) * std::tgamma(b + 1.0) * std::tgamma(c + 1.0));
+                    out.push_back((float)(mult * std::pow(d[3 * j], a) * std::pow(d[3 * j + 1], b) * std::pow(d[3 * j + 2], c)));
+                }
+            for (; k < KP; k++) out.push_back(0.f);
+            (void)K;
+        }
+    }
+    // nearest kProbeNbr probes of every probe, packed 4 per float slot
+    off[4] = out.size();
     std::vector<unsigned char> nb(kProbes * kProbeNbr);
     for (int i = 0; i < kProbes; i++) {
         double bd[kProbeNbr];
-        int bi[kProbeNbr], n = 0;
+        int bi[kProbeNbr], m = 0;
         for (int j = 0; j < kProbes; j++) {
             if (j == i) continue;
             double dot = std::fabs(d[3 * i] * d[3 * j] + d[3 * i + 1] * d[3 * j + 1] + d[3 * i + 2] * d[3 * j + 2]);
-            if (n == kProbeNbr && dot <= bd[kProbeNbr - 1]) continue;
-            int pos = n < kProbeNbr ? n++ : kProbeNbr - 1;
+            if (m == kProbeNbr && dot <= bd[kProbeNbr - 1]) continue;
+            int pos = m < kProbeNbr ? m++ : kProbeNbr - 1;
             while (pos > 0 && bd[pos - 1] < dot) { bd[pos] = bd[pos - 1]; bi[pos] = bi[pos - 1]; pos--; }
             bd[pos] = dot;
             bi[pos] = j;
         }
         for (int b = 0; b < kProbeNbr; b++) nb[i * kProbeNbr + b] = (unsigned char)bi[b];
     }
-    std::vector<float> df(d.begin(), d.end());
-    TTM_CUDA_TRY(cudaMemcpyToSymbol(c_dir, df.data(), df.size() * sizeof(float)));
-    TTM_CUDA_TRY(cudaMemcpyToSymbol(c_nbr, nb.data(), nb.size()));
-    for (int n : {2, 4, 6}) {
-        std::vector<float> phi;
-        for (int j = 0; j < kProbes; j++)
-            for (int a = n; a >= 0; a--)
-                for (int b = n - a; b >= 0; b--) {
-                    int c = n - a - b;
-                    double mult = std::tgamma(n + 1.0) / (std::tgamma(a + 1.0) * std::tgamma(b + 1.0) * std::tgamma(c + 1.0));
-                    double val = mult * std::pow(d[3 * j], a) * std::pow(d[3 * j + 1], b) * std::pow(d[3 * j + 2], c);
-                    phi.push_back((float)val);
-                }
-        if (n == 2) TTM_CUDA_TRY(cudaMemcpyToSymbol(c_phi2, phi.data(), phi.size() * sizeof(float)));
-        if (n == 4) TTM_CUDA_TRY(cudaMemcpyToSymbol(c_phi4, phi.data(), phi.size() * sizeof(float)));
-        if (n == 6) TTM_CUDA_TRY(cudaMemcpyToSymbol(c_phi6, phi.data(), phi.size() * sizeof(float)));
-    }
+    const size_t nfl = (nb.size() + 3) / 4;
+    out.resize(out.size() + nfl, 0.f);
+    std::memcpy(&out[off[4]], nb.data(), nb.size());
 }
 
-void peakmap_run(int n, const float* C, int64_t V, float* score, float* orient, float* frob, cudaStream_t st)
+void upload_probe_tables(ttm_ctx* ctx)
 {
-    const size_t smem = (size_t)kProbes * kPmThreads * sizeof(float);
-    const unsigned grid = (unsigned)ceil_div(V, kPmThreads);
+    std::vector<float> h;
+    size_t off[5];
+    build_probe_tables(h, off);
+    ctx->probe_tables.alloc(h.size() * sizeof(float));
+    TTM_CUDA_TRY(cudaMemcpy(ctx->probe_tables.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    for (int i = 0; i < 5; i++) ctx->probe_off[i] = off[i];
+}
+
+void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
+                 cudaStream_t st)
+{
+    const float* base = ctx->probe_tables.as<float>();
+    ProbeTables t{reinterpret_cast<const float4*>(base + ctx->probe_off[0]), base + ctx->probe_off[1],
+                  base + ctx->probe_off[2], base + ctx->probe_off[3],
+                  reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4])};
+    const int64_t blocks = ceil_div(V, kPmThreads);
+    const size_t smem = (size_t)kProbes * kPmThreads * sizeof(__half);
+    // enough CTAs to fill every SM several times, then a grid stride
+    const int64_t grid = std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 32);
+    // static tables + dynamic probe values can exceed the default 48 KB
+    // total, so the dynamic size is always declared
+#define TTM_PM_LAUNCH(N_)                                                                          \
+    TTM_CUDA_TRY(cudaFuncSetAttribute(k_peakmap<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_peakmap<N_><<<(unsigned)grid, kPmThreads, smem, st>>>(C, V, score, orient, frob, t);
     switch (n) {
-        case 2: set_smem(k_peakmap<2>, smem); k_peakmap<2><<<grid, kPmThreads, smem, st>>>(C, V, score, orient, frob); break;
-        case 4: set_smem(k_peakmap<4>, smem); k_peakmap<4><<<grid, kPmThreads, smem, st>>>(C, V, score, orient, frob); break;
-        case 6: set_smem(k_peakmap<6>, smem); k_peakmap<6><<<grid, kPmThreads, smem, st>>>(C, V, score, orient, frob); break;
+        case 2: TTM_PM_LAUNCH(2); break;
+        case 4: TTM_PM_LAUNCH(4); break;
+        case 6: TTM_PM_LAUNCH(6); break;
         default: throw Error{E_UNSUPPORTED, "order must be 2, 4 or 6"};
     }
+#undef TTM_PM_LAUNCH
     TTM_LAUNCH_CHECK();
 }
 
@@ -322,7 +499,7 @@ extern "C" ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximis
         const Prep& p = plan->prep;
         const int64_t V = (int64_t)p.Z * p.Y * p.X;
         stage_begin(plan, (cudaStream_t)stream);
-        peakmap_run(plan->fp.order_n, d_C, V, d_score, d_orient, d_frob, (cudaStream_t)stream);
+        peakmap_run(plan->ctx, plan->fp.order_n, d_C, V, d_score, d_orient, d_frob, (cudaStream_t)stream);
         stage_end(plan, ST_PEAKMAP, (cudaStream_t)stream);
         return TTM_OK;
     } catch (const Error& e) {

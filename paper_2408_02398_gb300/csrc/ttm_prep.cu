@@ -57,8 +57,10 @@ double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<doub
 constexpr int kPreThreads = 256;
 
 // One voxel per thread: g = h * f from the 27-point product filter in FP32
-// (the input is FP32), written as g (f32) and as (g, g^2) in FP64 for the
-// local sums; per-block partial sums of g^2 for the variance floor.
+// (the input is FP32), written as g (f32) and as (g, g^2) in FP64 or as
+// double-float pairs for the local sums; per-block partial sums of g^2 for
+// the variance floor.
+template <bool DF>
 __global__ void __launch_bounds__(kPreThreads)
 k_prefilter(const float* __restrict__ f, int Z, int Y, int X, float a, float* __restrict__ g32,
             double2* __restrict__ zc, double* __restrict__ partials)
@@ -89,8 +91,14 @@ k_prefilter(const float* __restrict__ f, int Z, int Y, int X, float a, float* __
             }
         }
         g32[v] = g;
-        const double gd = (double)g;
-        zc[v] = make_double2(gd, gd * gd);
+        if (DF) {
+            // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
+            const df64 sq = two_prod(g, g);
+            reinterpret_cast<float4*>(zc)[v] = make_float4(g, 0.f, sq.hi, sq.lo);
+        } else {
+            const double gd = (double)g;
+            zc[v] = make_double2(gd, gd * gd);
+        }
     }
     float sq = g * g;
 #pragma unroll
@@ -186,6 +194,49 @@ struct StoreW {
     }
 };
 
+// double-float versions of the mask-spectrum prologue and the w epilogue
+struct ProMaskSpectrumDF {
+    const float2* oct;
+    int Z, Y, X;
+    __device__ dcx operator()(dcx v, int64_t, int64_t i, int kz) const
+    {
+        int ky = (int)(i / X), kx = (int)(i - (int64_t)ky * X);
+        int az = kz <= Z - kz ? kz : Z - kz;
+        int ay = ky <= Y - ky ? ky : Y - ky;
+        int ax = kx <= X - kx ? kx : X - kx;
+        const float2 m2 = oct[((int64_t)az * (Y / 2 + 1) + ay) * (X / 2 + 1) + ax];
+        const df64 m(m2.x, m2.y);
+        dcx o;
+        o.x = v.x * m;
+        o.y = v.y * m;
+        return o;
+    }
+};
+
+struct StoreWDF {
+    float* w;
+    const double* floor;
+    df64 inv_M;
+    int X;
+    __device__ void operator()(dcx v, int64_t l, int64_t, int j) const
+    {
+        const df64 S1 = v.x, S2 = v.y;
+        const df64 var = S2 - (S1 * S1) * inv_M;  // the cancellation happens here, in double-float
+        const float vf = var.hi + var.lo;
+        const bool pos = vf > (float)floor[0] && vf > 1e-10f * (S2.hi + S2.lo);
+        w[l * X + j] = pos ? rsqrtf(vf) : 0.0f;
+    }
+};
+
+__global__ void k_octant_to_df(const double* __restrict__ in, int64_t n, float2* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = in[i];
+        const float h = (float)d;
+        out[i] = make_float2(h, (float)(d - (double)h));
+    }
+}
+
 // ---------------------------------------------------------------- host --
 
 void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
@@ -196,12 +247,15 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
     p.Z = Z; p.Y = Y; p.X = X; p.Xh = X / 2 + 1;
     p.tz = tz; p.ty = ty; p.tx = tx;
     p.filter_a = fp.filter_a;
-    p.px32 = make_len_plan(ctx->twiddles, X, false);
-    p.py32 = make_len_plan(ctx->twiddles, Y, false);
-    p.pz32 = make_len_plan(ctx->twiddles, Z, false);
-    p.px64 = make_len_plan(ctx->twiddles, X, true);
-    p.py64 = make_len_plan(ctx->twiddles, Y, true);
-    p.pz64 = make_len_plan(ctx->twiddles, Z, true);
+    p.px32 = make_len_plan(ctx->twiddles, X, TW_F32);
+    p.py32 = make_len_plan(ctx->twiddles, Y, TW_F32);
+    p.pz32 = make_len_plan(ctx->twiddles, Z, TW_F32);
+    p.px64 = make_len_plan(ctx->twiddles, X, TW_F64);
+    p.py64 = make_len_plan(ctx->twiddles, Y, TW_F64);
+    p.pz64 = make_len_plan(ctx->twiddles, Z, TW_F64);
+    p.pxd = make_len_plan(ctx->twiddles, X, TW_DF64);
+    p.pyd = make_len_plan(ctx->twiddles, Y, TW_DF64);
+    p.pzd = make_len_plan(ctx->twiddles, Z, TW_DF64);
     const int64_t V = (int64_t)Z * Y * X, Vh = (int64_t)Z * Y * p.Xh;
     p.nblk_pre = ceil_div(V, kPreThreads);
     p.g32.alloc(V * sizeof(float));
@@ -231,15 +285,23 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
                                ProIdentity<double>(), StoreTo<double>{spec, 0, (int64_t)Y * p.Xh}, st);
     k_mhat_octant<<<1024, 256, 0, st>>>(spec, Z, Y, p.Xh, X, 1.0 / (double)V, p.mhat.as<double>());
     TTM_LAUNCH_CHECK();
+    p.mhat_df.alloc(noct * sizeof(float2));
+    k_octant_to_df<<<1024, 256, 0, st>>>(p.mhat.as<double>(), noct, p.mhat_df.as<float2>());
+    TTM_LAUNCH_CHECK();
     TTM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st)
 {
     const int64_t V = (int64_t)p.Z * p.Y * p.X;
-    k_prefilter<<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
-                                                           p.g32.as<float>(), p.zc.as<double2>(),
-                                                           p.partials.as<double>());
+    if (p.localsum_mode == 1)
+        k_prefilter<true><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
+                                                                     p.g32.as<float>(), p.zc.as<double2>(),
+                                                                     p.partials.as<double>());
+    else
+        k_prefilter<false><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
+                                                                      p.g32.as<float>(), p.zc.as<double2>(),
+                                                                      p.partials.as<double>());
     TTM_LAUNCH_CHECK();
     k_var_floor<<<1, 1024, 0, st>>>(p.partials.as<double>(), p.nblk_pre, V, p.M, p.floor.as<double>());
     TTM_LAUNCH_CHECK();
@@ -257,24 +319,39 @@ void prep_spectrum(Prep& p, cudaStream_t st)
                               ProIdentity<float>(), StoreTo<float>{G, 0, (int64_t)Y * Xh}, st);
 }
 
-// local sums in FP64: forward x, y, z of (g + i g^2), times the mask
-// spectrum, inverse z, y, x with the w epilogue
+// local sums: forward x, y, z of (g + i g^2), times the mask spectrum,
+// inverse z, y, x with the w epilogue; in FP64 or in double-float
 void prep_localsums(Prep& p, cudaStream_t st)
 {
     const int Z = p.Z, Y = p.Y, X = p.X;
-    double2* zc = p.zc.as<double2>();
     const int64_t YX = (int64_t)Y * X;
+    if (p.localsum_mode == 1) {
+        dcx* zd = p.zc.as<dcx>();
+        launch_contig_any<df64, -1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(), StoreTo<df64>{zd, X, 1}, st);
+        launch_strided_any<df64, -1>(zd, StridedAxis{X, Z, YX, X}, p.pyd, ProIdentity<df64>(),
+                                     StoreTo<df64>{zd, YX, X}, st);
+        launch_strided_any<df64, -1>(zd, StridedAxis{YX, 1, 0, YX}, p.pzd, ProIdentity<df64>(),
+                                     StoreTo<df64>{zd, 0, YX}, st);
+        launch_strided_any<df64, +1>(zd, StridedAxis{YX, 1, 0, YX}, p.pzd,
+                                     ProMaskSpectrumDF{p.mhat_df.as<float2>(), Z, Y, X}, StoreTo<df64>{zd, 0, YX}, st);
+        launch_strided_any<df64, +1>(zd, StridedAxis{X, Z, YX, X}, p.pyd, ProIdentity<df64>(),
+                                     StoreTo<df64>{zd, YX, X}, st);
+        launch_contig_any<df64, +1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(),
+                                    StoreWDF{p.w.as<float>(), p.floor.as<double>(), df64(1.0 / p.M), X}, st);
+        return;
+    }
+    double2* zc = p.zc.as<double2>();
     launch_contig_any<double, -1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(), StoreTo<double>{zc, X, 1}, st);
     launch_strided_any<double, -1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
-                               StoreTo<double>{zc, YX, X}, st);
+                                   StoreTo<double>{zc, YX, X}, st);
     launch_strided_any<double, -1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64, ProIdentity<double>(),
-                               StoreTo<double>{zc, 0, YX}, st);
+                                   StoreTo<double>{zc, 0, YX}, st);
     launch_strided_any<double, +1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64,
-                               ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, StoreTo<double>{zc, 0, YX}, st);
+                                   ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, StoreTo<double>{zc, 0, YX}, st);
     launch_strided_any<double, +1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
-                               StoreTo<double>{zc, YX, X}, st);
+                                   StoreTo<double>{zc, YX, X}, st);
     launch_contig_any<double, +1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(),
-                              StoreW{p.w.as<float>(), p.floor.as<double>(), p.M, X}, st);
+                                  StoreW{p.w.as<float>(), p.floor.as<double>(), p.M, X}, st);
 }
 
 }  // namespace ttm

@@ -67,7 +67,7 @@ struct SinkTMMax {
     __device__ void operator()(int, int64_t row, int x, float v) const
     {
         int64_t i = row * X + x;
-        float c = w[i] * v;
+        float c = __ldg(w + i) * v;
         if (c > best[i]) { best[i] = c; best_idx[i] = j; }
     }
 };

@@ -21,13 +21,14 @@ STATUS = {0: "TTM_OK", 1: "TTM_E_INVALID_ARG", 2: "TTM_E_SHAPE", 3: "TTM_E_UNSUP
           5: "TTM_E_CUDA", 6: "TTM_E_TIMEOUT", 7: "TTM_E_INTERNAL"}
 TTM_PREC_FP32, TTM_PREC_FP16_SPECTRA, TTM_PREC_BF16_SPECTRA = 0, 1, 2
 TTM_MAX_PLAIN, TTM_MAX_MLP_WARM = 0, 1
+TTM_LOCALSUM_FP64, TTM_LOCALSUM_DF64 = 0, 1
 
 # every symbol include/ttm.h declares
 EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_error", "ttm_num_components",
            "ttm_version", "ttm_rotation_set", "ttm_build_tensor_field", "ttm_plan_create", "ttm_plan_destroy",
            "ttm_plan_components", "ttm_plan_valid_box", "ttm_correlate", "ttm_plan_copy_w", "ttm_peak_map",
            "ttm_find_peaks", "tm_correlate", "ttm_plan_enable_timing", "ttm_plan_stage_times", "ttm_num_stages",
-           "ttm_stage_name", "ttm_kernel_launches"]
+           "ttm_stage_name", "ttm_kernel_launches", "ttm_plan_set_localsum"]
 
 
 class TTMError(RuntimeError):
@@ -80,6 +81,7 @@ def lib():
             "ttm_num_stages": (_i, []),
             "ttm_stage_name": (C.c_char_p, [_i]),
             "ttm_kernel_launches": (C.c_uint64, []),
+            "ttm_plan_set_localsum": (_i, [_vp, _i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -213,6 +215,10 @@ def ttm_correlate(plan: Plan, d_tomo, d_C, stream=None):
     import torch
     plan.ctx.check(lib().ttm_correlate(plan.h, _dev(d_tomo, torch.float32, "d_tomo"),
                                        _dev(d_C, torch.float32, "d_C"), _stream(stream)))
+
+
+def ttm_plan_set_localsum(plan: Plan, mode: int):
+    plan.ctx.check(lib().ttm_plan_set_localsum(plan.h, int(mode)))
 
 
 def ttm_plan_copy_w(plan: Plan, d_w, stream=None):
