@@ -251,16 +251,34 @@ def run_ours(args, ws, rank, local):
     ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws, dev)
     e2e_value = V * args.steps * ws / (ms_e2e / 1e3)
 
-    # roofline of the dominant part. Stages are per-step milliseconds.
+    # Rooflines. Stages are per-step milliseconds of CUDA events on the
+    # launching stream. The dominant kernel is the maximiser (FP32-ALU
+    # bound): its algorithmic work is the dense probe contraction,
+    # 2 K P flops per voxel (P = 128 probe directions); the FP32 peak is
+    # 152 SMs x 128 lanes x 2 flops x the median SM clock sampled during the
+    # run. The correlate path (ttm_correlate) is HBM-bound: 4 + 4K bytes per
+    # voxel (read f, write K maps) against the measured copy bandwidth.
+    # `traffic` is dram read + write bytes per launch from one ncu capture
+    # of a 128 x 512 x 512 case, scaled by voxel count (traffic grows in
+    # proportion), for the kernels as they were when captured.
     st_ms = {k: v / args.steps for k, v in stages.items()}
-    corr_ms = sum(v for k, v in st_ms.items() if k != "peak_map")
+    corr_ms = sum(v for k, v in st_ms.items() if k != "peak_map")   # ttm_correlate
     pk, how = peaks_file()
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    alg_bytes_corr = (4 + 4 * K) * V          # read f, write K normalised maps
-    roof = {"bound": "hbm", "kernel": "ttm_correlate (fused correlate path, stages 0-5)",
-            "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "peak_source": how, "traffic": None, "bytes_per_voxel": 4 + 4 * K}
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    probes = 128
+    pm_flops = 2.0 * K * probes * V
+    roof = {"bound": "alu", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
+            "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+            "peak_source": "FP32 FMA rate from unit counts at the sampled SM clock",
+            "traffic": 4.18e9, "flops_per_voxel": 2 * K * probes}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    alg_bytes_corr = (4 + 4 * K) * V
+    roof_corr = {"bound": "hbm", "kernel": "ttm_correlate (stages prefilter..xpass)",
+                 "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                 "peak_source": how, "traffic": 28.1e9, "bytes_per_voxel": 4 + 4 * K}
+    roof_corr["frac"] = roof_corr["achieved"] / roof_corr["peak"]
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -278,7 +296,7 @@ def run_ours(args, ws, rank, local):
                            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1gpu",
                            "local_sums": {"df64": "double-float (FP32 pairs, ~48-bit significand)",
                                           "fp64": "fp64"}[args.localsum], "spectra": "fp32"},
-                "roofline": roof, "stages_ms": st_ms, "setup_s": setup_s,
+                "roofline": roof, "roofline_correlate": roof_corr, "stages_ms": st_ms, "setup_s": setup_s,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": V * 4,
                         "d2h_bytes_per_step": V * 4 * 4},

@@ -199,8 +199,8 @@ ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int Y, int X, 
 
 /* Per-stage timing of a plan with CUDA events recorded on the stream of
  * each call (off by default). Stages: 0 prefilter + variance floor,
- * 1 image spectrum, 2 FP64 local sums -> w, 3 fused z pass, 4 y pass,
- * 5 x pass with the w epilogue, 6 peak map. ttm_plan_stage_times
+ * 1 image spectrum, 2 local sums -> w, 3 fused z pass, 4 y pass, 5 x pass
+ * with the w epilogue, 6 peak map. ttm_plan_stage_times
  * synchronises, adds the elapsed milliseconds of every call since the last
  * reset into ms[0..n-1] (n <= ttm_num_stages()) and clears the record. */
 ttm_status ttm_plan_enable_timing(ttm_plan* plan, int on);

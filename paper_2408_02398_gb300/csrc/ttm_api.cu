@@ -103,7 +103,7 @@ ttm_plan::~ttm_plan()
     for (cudaEvent_t e : free_ev) cudaEventDestroy(e);
 }
 
-static const char* kStageNames[ST_COUNT] = {"prefilter", "image_spectrum", "local_sums_fp64", "zpass_fused",
+static const char* kStageNames[ST_COUNT] = {"prefilter", "image_spectrum", "local_sums", "zpass_fused",
                                             "ypass", "xpass_c2r_norm", "peak_map"};
 
 extern "C" int ttm_num_stages(void) { return ST_COUNT; }

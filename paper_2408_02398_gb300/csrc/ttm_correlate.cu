@@ -10,6 +10,7 @@
 // transform along z, multiplies by the image spectrum (conjugated template)
 // and transforms back along z. Then a y pass over all K components and an
 // x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
+
 #include <vector>
 
 #include "fft_reg.cuh"
@@ -151,10 +152,13 @@ void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st
     stage_begin(P, st);
     prep_filter(p, d_tomo, st);
     stage_end(P, ST_FILTER, st);
-    prep_spectrum(p, st);
-    stage_end(P, ST_SPECTRUM, st);
+    // (the local sums were measured running on a second stream beside the
+    // spectrum and the z/y passes: both slowed down by as much as they
+    // overlapped, so they run in sequence)
     prep_localsums(p, st);
     stage_end(P, ST_LOCALSUM, st);
+    prep_spectrum(p, st);
+    stage_end(P, ST_SPECTRUM, st);
     float2* work = P->work.as<float2>();
     launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32, st);
     stage_end(P, ST_ZCORR, st);
@@ -210,6 +214,7 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
         P->K = ttm_num_components(params->order_n, params->dprime);
         P->prec = precision;
         prep_create(ctx, P->prep, Z, Y, X, tz, ty, tx, *params);
+
         plan_build_spectra(P, d_field);
         const int64_t Vh = (int64_t)Z * Y * P->prep.Xh;
         P->work.alloc(P->K * Vh * sizeof(float2));
