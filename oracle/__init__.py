@@ -70,6 +70,8 @@ def _declare(L):
         "oracle_find_peaks": (_i, [_pd, _i, _i, _i, _i, _i, _i, _i, _i, _i, _i, _d, _pi64, _pd]),
         "oracle_tm": (None, [_pd, _i, _i, _i, _pd, _i, _i, _i, _pd, _i64, _i, _pi64, _i64, _pd,
                              _pd, _pi32]),
+        "oracle_mlp_num_params": (_i64, [_i, _i]),
+        "oracle_mlp": (_d, [_pd, _i, _i, _pd, _pd, _i64, _pd, _pd]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -338,6 +340,25 @@ def tm(g, tp, quats, vox=None, periodic: bool = False, w=None):
     lib().oracle_tm(_p(g), Z, Y, X, _p(tp), tz, ty, tx, _p(quats), quats.shape[0],
                     int(periodic), _p(v, _pi64), v.size, _p(wv), _p(best), _p(bidx, _pi32))
     return best, bidx
+
+
+# ------------------------------------------------------- learned start ---
+
+def mlp_num_params(K: int, H: int = 128) -> int:
+    return int(lib().oracle_mlp_num_params(K, H))
+
+
+def mlp(params, X, U=None, H: int = 128, want_grad: bool = False):
+    """MLP K -> H -> H -> 3 (GELU), normalised output: returns (u_hat [n][3],
+    summed loss 1 - (u_hat . u*)^2 or None, summed gradient or None)."""
+    params = _f64(params)
+    X = _f64(X)
+    n, K = X.shape
+    Ud = None if U is None else _f64(U)
+    out = np.zeros((n, 3))
+    grad = np.zeros(params.size) if want_grad else None
+    loss = lib().oracle_mlp(_p(params), K, H, _p(X), _p(Ud), n, _p(out), _p(grad))
+    return out, (loss if U is not None else None), grad
 
 
 # ------------------------------------------------------------ pipelines ---

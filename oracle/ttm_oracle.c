@@ -956,3 +956,112 @@ ORACLE_API void oracle_tm(const double* g, int Z, int Y, int X, const double* tp
     free(rot);
     free(c);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (reference for the GPU training and inference): an MLP
+ * K -> H -> H -> 3 with GELU activations in their tanh form,
+ * GELU(x) = x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) / 2,
+ * whose output y is normalised, u_hat = y/|y|,
+ * to predict the maximising direction of p_x from the components scaled to
+ * unit Frobenius norm. Loss per sample: 1 - (u_hat . u*)^2, which does not
+ * depend on the sign of u* (the maximiser is defined up to sign).
+ * Parameters, flat: W1 [H][K], b1 [H], W2 [H][H], b2 [H], W3 [3][H], b3 [3]. */
+
+static double gelu(double x)
+{
+    const double c = sqrt(2.0 / PI);
+    return 0.5 * x * (1.0 + tanh(c * (x + 0.044715 * x * x * x)));
+}
+/* derivative of the tanh form: with t = tanh(c (x + 0.044715 x^3)),
+ * GELU'(x) = (1 + t)/2 + x (1 - t^2) c (1 + 3 * 0.044715 x^2) / 2 */
+static double gelu_grad(double x)
+{
+    const double c = sqrt(2.0 / PI);
+    const double t = tanh(c * (x + 0.044715 * x * x * x));
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * c * (1.0 + 3.0 * 0.044715 * x * x);
+}
+
+ORACLE_API int64_t oracle_mlp_num_params(int K, int H) { return (int64_t)H * K + H + H * H + H + 3 * H + 3; }
+
+/* forward for n samples; out = u_hat [n][3]; loss (sum over samples) if
+ * U != NULL; grad (sum over samples, same layout as params) if grad != NULL */
+ORACLE_API double oracle_mlp(const double* params, int K, int H, const double* X, const double* U, int64_t n,
+                             double* out, double* grad)
+{
+    const double* W1 = params;
+    const double* b1 = W1 + (size_t)H * K;
+    const double* W2 = b1 + H;
+    const double* b2 = W2 + (size_t)H * H;
+    const double* W3 = b2 + H;
+    const double* b3 = W3 + 3 * H;
+    double *gW1 = NULL, *gb1 = NULL, *gW2 = NULL, *gb2 = NULL, *gW3 = NULL, *gb3 = NULL;
+    if (grad) {
+        memset(grad, 0, sizeof(double) * oracle_mlp_num_params(K, H));
+        gW1 = grad; gb1 = gW1 + (size_t)H * K; gW2 = gb1 + H; gb2 = gW2 + (size_t)H * H; gW3 = gb2 + H; gb3 = gW3 + 3 * H;
+    }
+    double* a1 = (double*)malloc(sizeof(double) * H);
+    double* h1 = (double*)malloc(sizeof(double) * H);
+    double* a2 = (double*)malloc(sizeof(double) * H);
+    double* h2 = (double*)malloc(sizeof(double) * H);
+    double* d2 = (double*)malloc(sizeof(double) * H);
+    double* d1 = (double*)malloc(sizeof(double) * H);
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; s++) {
+        const double* x = X + (size_t)s * K;
+        for (int i = 0; i < H; i++) {
+            double acc = b1[i];
+            for (int k = 0; k < K; k++) acc += W1[(size_t)i * K + k] * x[k];
+            a1[i] = acc;
+            h1[i] = gelu(acc);
+        }
+        for (int i = 0; i < H; i++) {
+            double acc = b2[i];
+            for (int k = 0; k < H; k++) acc += W2[(size_t)i * H + k] * h1[k];
+            a2[i] = acc;
+            h2[i] = gelu(acc);
+        }
+        double y[3];
+        for (int c = 0; c < 3; c++) {
+            double acc = b3[c];
+            for (int k = 0; k < H; k++) acc += W3[(size_t)c * H + k] * h2[k];
+            y[c] = acc;
+        }
+        double ny = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+        double uh[3] = {y[0] / ny, y[1] / ny, y[2] / ny};
+        if (out) for (int c = 0; c < 3; c++) out[(size_t)s * 3 + c] = uh[c];
+        if (!U) continue;
+        const double* us = U + (size_t)s * 3;
+        double dot = uh[0] * us[0] + uh[1] * us[1] + uh[2] * us[2];
+        loss += 1.0 - dot * dot;
+        if (!grad) continue;
+        /* dL/du_hat = -2 dot u*; dL/dy = (I - u_hat u_hat^T) dL/du_hat / |y| */
+        double gu[3] = {-2.0 * dot * us[0], -2.0 * dot * us[1], -2.0 * dot * us[2]};
+        double ug = uh[0] * gu[0] + uh[1] * gu[1] + uh[2] * gu[2];
+        double gy[3];
+        for (int c = 0; c < 3; c++) gy[c] = (gu[c] - ug * uh[c]) / ny;
+        for (int c = 0; c < 3; c++) {
+            gb3[c] += gy[c];
+            for (int k = 0; k < H; k++) gW3[(size_t)c * H + k] += gy[c] * h2[k];
+        }
+        for (int k = 0; k < H; k++) {
+            double g = 0.0;
+            for (int c = 0; c < 3; c++) g += W3[(size_t)c * H + k] * gy[c];
+            d2[k] = g * gelu_grad(a2[k]);
+        }
+        for (int i = 0; i < H; i++) {
+            gb2[i] += d2[i];
+            for (int k = 0; k < H; k++) gW2[(size_t)i * H + k] += d2[i] * h1[k];
+        }
+        for (int k = 0; k < H; k++) {
+            double g = 0.0;
+            for (int i = 0; i < H; i++) g += W2[(size_t)i * H + k] * d2[i];
+            d1[k] = g * gelu_grad(a1[k]);
+        }
+        for (int i = 0; i < H; i++) {
+            gb1[i] += d1[i];
+            for (int k = 0; k < K; k++) gW1[(size_t)i * K + k] += d1[i] * x[k];
+        }
+    }
+    free(a1); free(h1); free(a2); free(h2); free(d2); free(d1);
+    return loss;
+}

@@ -535,3 +535,46 @@ def test_ttm_invariant_under_quarter_turns_of_the_tomogram():
     u0 = base["orient"] @ P.T
     dots = np.abs(np.sum(u0[ok] * moved["orient"][j][ok], axis=1))
     assert np.all(dots > 1 - 1e-9)
+
+
+# -------------------------------------------------------- learned start --
+
+def test_mlp_gradient_matches_finite_differences():
+    """Backward pass of the MLP reference against central differences of its
+    own loss (relative 1e-6)."""
+    K, H = 7, 9
+    rng = np.random.default_rng(11)
+    P = rng.normal(size=O.mlp_num_params(K, H)) * 0.6
+    X = rng.normal(size=(6, K))
+    U = rng.normal(size=(6, 3))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    _, L, g = O.mlp(P, X, U, H=H, want_grad=True)
+    eps = 1e-6
+    fd = np.empty_like(g)
+    for i in range(P.size):
+        e = np.zeros_like(P)
+        e[i] = eps
+        fd[i] = (O.mlp(P + e, X, U, H=H)[1] - O.mlp(P - e, X, U, H=H)[1]) / (2 * eps)
+    assert np.abs(fd - g).max() <= 1e-6 * max(1.0, np.abs(g).max())
+
+
+def test_mlp_closed_form_and_sign_invariance():
+    """One hidden unit: y = (GELU(GELU(x)), 0, 0) + (0, 1, 0), so
+    u_hat = (g, 1, 0) / sqrt(g^2 + 1) with GELU written out independently;
+    the loss 1 - (u_hat . u*)^2 is the same for u* and -u*."""
+    K, H = 1, 1
+    # W1, b1, W2, b2, W3 (3x1), b3
+    P = np.array([1.0, 0.0, 1.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0])
+    gelu = lambda x: 0.5 * x * (1 + math.tanh(math.sqrt(2 / math.pi) * (x + 0.044715 * x ** 3)))
+    for x in (-1.3, 0.0, 0.7, 2.5):
+        g = gelu(gelu(x))
+        u, _, _ = O.mlp(P, np.array([[x]]), H=H)
+        assert np.allclose(u[0], np.array([g, 1.0, 0.0]) / math.hypot(g, 1.0), atol=1e-15)
+    rng = np.random.default_rng(2)
+    Pr = rng.normal(size=O.mlp_num_params(5, 4))
+    X = rng.normal(size=(3, 5))
+    U = rng.normal(size=(3, 3))
+    _, L1, g1 = O.mlp(Pr, X, U, H=4, want_grad=True)
+    _, L2, g2 = O.mlp(Pr, X, -U, H=4, want_grad=True)
+    assert L1 == pytest.approx(L2, rel=1e-14)
+    assert np.allclose(g1, g2, atol=1e-14)
