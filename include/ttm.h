@@ -181,6 +181,32 @@ ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, co
 ttm_status ttm_find_peaks(ttm_plan* plan, const float* d_map, int P, double min_dist,
                           int64_t* h_idx, float* h_val, int* h_count, void* stream);
 
+/* Allocation-free Find Peaks. The paper has no counterpart to this entry
+ * point: it returns exactly what ttm_find_peaks returns for the same map,
+ * box, P and min_dist, but allocates no memory, device or library, and needs
+ * no plan. It serves callers that cannot allocate device memory where they
+ * need peaks: a process whose free device memory is reserved by another
+ * allocator (a framework's caching pool), or a streaming loop in which
+ * cudaMalloc / cudaFree would synchronise the device and stall the work on
+ * other streams.
+ *   d_map    float32 [Z][Y][X] (device)
+ *   box      host int[6]: z0, z1, y0, y1, x0, x1 (half-open), the search
+ *            region (ttm_plan_valid_box gives the valid box of a plan)
+ *   h_idx, h_val, h_count: as ttm_find_peaks (host; room for P entries)
+ * Scratch is one fixed device array inside the library (about 3.3 MB per
+ * device): at most 262144 local maxima in the box and P <= 16384. A larger
+ * P, or a map with more local maxima in the box, fails with TTM_E_SHAPE
+ * (nothing written to h_idx / h_val). The first call on a device does a
+ * one-time set-up (it looks up the device address of that array with the
+ * device current); make that first call before any stream capture begins.
+ * Every call clears the array's candidate counter on `stream` before use.
+ * All calls on one device share the array: calls that overlap (on other
+ * streams or host threads) race and must be serialised by the caller.
+ * Synchronises `stream`. */
+ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, int Z, int Y, int X,
+                                  const int* box, int P, double min_dist, int64_t* h_idx,
+                                  float* h_val, int* h_count, void* stream);
+
 /* ------------------------------------------------------- step a6: Eqs. 1, 6, 7 */
 
 /* Classical template matching baseline: for every rotation q_j of h_quats

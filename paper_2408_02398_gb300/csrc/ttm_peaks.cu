@@ -4,6 +4,8 @@
 // index) and compacts them; the host orders the candidates by (value desc,
 // index asc) and accepts greedily.
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "ttm_internal.h"
@@ -107,5 +109,205 @@ extern "C" ttm_status ttm_find_peaks(ttm_plan* plan, const float* d_map, int P, 
         return TTM_OK;
     } catch (const Error& e) {
         return (ttm_status)fail(plan->ctx, e);
+    }
+}
+
+// ----------------------------------------------------------------------
+// Allocation-free Find Peaks. Same result as ttm_find_peaks, for callers
+// that cannot allocate device memory at the point where they need peaks:
+// a process whose free device memory is already reserved by another
+// allocator (a framework's caching pool that holds the HBM it once used),
+// or a streaming loop in which cudaMalloc / cudaFree would synchronise the
+// device and stall the work queued on other streams. It also needs no
+// plan: ttm_find_peaks takes its candidate buffer from a plan, and
+// creating a plan allocates the whole correlate workspace.
+//
+// The scratch lives in one file-scope device array of fixed size: at most
+// kStaticCand local maxima (26-neighbour, inside the box) and at most
+// kStaticPeaks accepted peaks. Larger requests are rejected with
+// TTM_E_SHAPE. The array is shared by every call on a device, so calls that
+// overlap (other streams, other host threads) race on it and must be
+// serialised by the caller.
+//
+// Device work: the compaction kernel above writes the candidates, then one
+// CTA repeats "take the best remaining candidate (value desc, index asc),
+// remove those closer than min_dist" P times. Taking the best remaining
+// candidate that no accepted peak suppresses is exactly the greedy pass over
+// the sorted candidate list, so the accepted list equals ttm_find_peaks'.
+namespace ttm {
+
+constexpr int64_t kStaticCand = int64_t(1) << 18;  // 262144 candidates
+constexpr int kStaticPeaks = 16384;
+constexpr size_t kOffCandIdx = 0;                                        // int64 [kStaticCand]
+constexpr size_t kOffCandVal = kOffCandIdx + sizeof(int64_t) * kStaticCand;  // float [kStaticCand]
+constexpr size_t kOffOutIdx = kOffCandVal + sizeof(float) * kStaticCand;     // int64 [kStaticPeaks]
+constexpr size_t kOffOutVal = kOffOutIdx + sizeof(int64_t) * kStaticPeaks;   // float [kStaticPeaks]
+constexpr size_t kOffCount = kOffOutVal + sizeof(float) * kStaticPeaks;      // u64 candidate counter
+constexpr size_t kOffOutCount = kOffCount + 256;                             // int accepted count
+constexpr size_t kStaticScratchBytes = kOffOutCount + 256;                   // 3,342,848 bytes
+static_assert(kOffCandVal % 256 == 0 && kOffOutIdx % 256 == 0 && kOffOutVal % 256 == 0 && kOffCount % 256 == 0,
+              "scratch parts must stay 256-byte aligned");
+
+static __device__ __align__(256) unsigned char g_peak_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+// One-time set-up per device, with that device current: the device address
+// of g_peak_scratch in this device's copy of the module.
+static unsigned char* static_scratch(int device)
+{
+    TTM_REQUIRE(device >= 0 && device < kMaxDevices, E_UNSUPPORTED, "device ordinal beyond the static scratch table");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_peak_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error{E_CUDA, std::string("cudaGetSymbolAddress(peak scratch): ") + cudaGetErrorString(e)};
+        g_scratch_addr[device] = static_cast<unsigned char*>(p);
+    }
+    return g_scratch_addr[device];
+}
+
+struct Best {
+    float v;
+    int64_t i, pos;  // pos < 0: none
+};
+
+__device__ __forceinline__ bool better(const Best& a, const Best& b)
+{
+    if (a.pos < 0) return false;
+    if (b.pos < 0) return true;
+    if (a.v != b.v) return a.v > b.v;
+    return a.i < b.i;
+}
+
+__device__ __forceinline__ Best shfl_best(const Best& b, int off)
+{
+    Best o;
+    o.v = __shfl_down_sync(0xffffffffu, b.v, off);
+    o.i = __shfl_down_sync(0xffffffffu, b.i, off);
+    o.pos = __shfl_down_sync(0xffffffffu, b.pos, off);
+    return o;
+}
+
+// Greedy selection over the compacted candidates (one CTA). Removed
+// candidates get index -1. *out_count = accepted peaks, or -1 when the
+// candidates overflowed the scratch.
+__global__ void __launch_bounds__(1024) k_select_greedy(const unsigned long long* __restrict__ count, int64_t cap,
+                                                        int P, double md2, int64_t X, int64_t Y,
+                                                        int64_t* __restrict__ cidx, const float* __restrict__ cval,
+                                                        int64_t* __restrict__ oidx, float* __restrict__ oval,
+                                                        int* __restrict__ out_count)
+{
+    __shared__ Best warp_best[32];
+    __shared__ Best chosen;
+    const unsigned long long nn = *count;
+    if (nn > (unsigned long long)cap) {
+        if (threadIdx.x == 0) *out_count = -1;
+        return;
+    }
+    const int64_t n = (int64_t)nn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    bool have = false;
+    double az = 0, ay = 0, ax = 0;
+    int got = 0;
+    for (int it = 0; it < P; it++) {
+        Best b{0.f, 0, -1};
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+            const int64_t i = cidx[k];
+            if (i < 0) continue;
+            if (have) {
+                const double x = (double)(i % X), y = (double)((i / X) % Y), z = (double)(i / (X * Y));
+                const double dz = z - az, dy = y - ay, dx = x - ax;
+                if (dz * dz + dy * dy + dx * dx < md2) {
+                    cidx[k] = -1;
+                    continue;
+                }
+            }
+            const Best c{cval[k], i, k};
+            if (better(c, b)) b = c;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const Best o = shfl_best(b, off);
+            if (better(o, b)) b = o;
+        }
+        if (lane == 0) warp_best[warp] = b;
+        __syncthreads();
+        if (warp == 0) {
+            b = lane < nwarps ? warp_best[lane] : Best{0.f, 0, -1};
+            for (int off = 16; off > 0; off >>= 1) {
+                const Best o = shfl_best(b, off);
+                if (better(o, b)) b = o;
+            }
+            if (lane == 0) {
+                chosen = b;
+                if (b.pos >= 0) {
+                    oidx[it] = b.i;
+                    oval[it] = b.v;
+                    cidx[b.pos] = -1;
+                }
+            }
+        }
+        __syncthreads();
+        const Best c = chosen;
+        if (c.pos < 0) break;
+        got++;
+        have = true;
+        ax = (double)(c.i % X);
+        ay = (double)((c.i / X) % Y);
+        az = (double)(c.i / (X * Y));
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out_count = got;
+}
+
+}  // namespace ttm
+
+extern "C" ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, int Z, int Y, int X, const int* box,
+                                             int P, double min_dist, int64_t* h_idx, float* h_val, int* h_count,
+                                             void* stream)
+{
+    if (!ctx) return TTM_E_INVALID_ARG;
+    try {
+        TTM_REQUIRE(d_map && box && h_idx && h_val && h_count && Z > 0 && Y > 0 && X > 0 && P >= 0 && min_dist >= 0,
+                    E_INVALID_ARG, "bad argument");
+        TTM_REQUIRE(box[0] >= 0 && box[0] <= box[1] && box[1] <= Z && box[2] >= 0 && box[2] <= box[3] &&
+                        box[3] <= Y && box[4] >= 0 && box[4] <= box[5] && box[5] <= X,
+                    E_INVALID_ARG, "box must satisfy 0 <= lo <= hi <= extent on every axis");
+        TTM_REQUIRE(P <= kStaticPeaks, E_SHAPE, "P exceeds the static peak capacity of 16384");
+        *h_count = 0;
+        if (P == 0) return TTM_OK;
+        TTM_CUDA_TRY(cudaSetDevice(ctx->device));
+        unsigned char* s = static_scratch(ctx->device);
+        cudaStream_t st = (cudaStream_t)stream;
+        int64_t* cidx = reinterpret_cast<int64_t*>(s + kOffCandIdx);
+        float* cval = reinterpret_cast<float*>(s + kOffCandVal);
+        int64_t* oidx = reinterpret_cast<int64_t*>(s + kOffOutIdx);
+        float* oval = reinterpret_cast<float*>(s + kOffOutVal);
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s + kOffCount);
+        int* ocnt = reinterpret_cast<int*>(s + kOffOutCount);
+        // the candidate counter must start at zero on every call
+        TTM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+        k_localmax<<<4 * 152 * 8, 256, 0, st>>>(d_map, Z, Y, X, box[0], box[1], box[2], box[3], box[4], box[5],
+                                               kStaticCand, cidx, cval, cnt);
+        TTM_LAUNCH_CHECK();
+        k_select_greedy<<<1, 1024, 0, st>>>(cnt, kStaticCand, P, min_dist * min_dist, X, Y, cidx, cval, oidx, oval,
+                                            ocnt);
+        TTM_LAUNCH_CHECK();
+        int got = 0;
+        TTM_CUDA_TRY(cudaMemcpyAsync(&got, ocnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        TTM_REQUIRE(got >= 0, E_SHAPE, "more than 262144 local maxima in the box: beyond the static candidate capacity");
+        if (got > 0) {
+            TTM_CUDA_TRY(cudaMemcpyAsync(h_idx, oidx, got * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            TTM_CUDA_TRY(cudaMemcpyAsync(h_val, oval, got * sizeof(float), cudaMemcpyDeviceToHost, st));
+            TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        *h_count = got;
+        return TTM_OK;
+    } catch (const Error& e) {
+        return (ttm_status)fail(ctx, e);
     }
 }

@@ -28,7 +28,8 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_
            "ttm_version", "ttm_rotation_set", "ttm_build_tensor_field", "ttm_plan_create", "ttm_plan_destroy",
            "ttm_plan_components", "ttm_plan_valid_box", "ttm_correlate", "ttm_plan_copy_w", "ttm_peak_map",
            "ttm_find_peaks", "tm_correlate", "ttm_plan_enable_timing", "ttm_plan_stage_times", "ttm_num_stages",
-           "ttm_stage_name", "ttm_kernel_launches", "ttm_plan_set_localsum"]
+           "ttm_stage_name", "ttm_kernel_launches", "ttm_plan_set_localsum",
+           "ttm_find_peaks_noalloc"]
 
 
 class TTMError(RuntimeError):
@@ -82,6 +83,7 @@ def lib():
             "ttm_stage_name": (C.c_char_p, [_i]),
             "ttm_kernel_launches": (C.c_uint64, []),
             "ttm_plan_set_localsum": (_i, [_vp, _i]),
+            "ttm_find_peaks_noalloc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _d, _vp, _vp, C.POINTER(_i), _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -242,6 +244,20 @@ def ttm_find_peaks(plan: Plan, d_map, P: int, min_dist: float, stream=None):
     n = C.c_int(0)
     plan.ctx.check(lib().ttm_find_peaks(plan.h, _dev(d_map, torch.float32, "d_map"), P, float(min_dist),
                                         idx.ctypes.data, val.ctypes.data, C.byref(n), _stream(stream)))
+    return idx[:n.value], val[:n.value]
+
+
+def ttm_find_peaks_noalloc(ctx: Context, d_map, box, P: int, min_dist: float, stream=None):
+    """Allocation-free Find Peaks over box (z0, z1, y0, y1, x0, x1) of d_map."""
+    import torch
+    Z, Y, X = d_map.shape
+    b = (C.c_int * 6)(*[int(v) for v in box])
+    idx = np.zeros(max(P, 1), dtype=np.int64)
+    val = np.zeros(max(P, 1), dtype=np.float32)
+    n = C.c_int(0)
+    ctx.check(lib().ttm_find_peaks_noalloc(ctx.h, _dev(d_map, torch.float32, "d_map"), Z, Y, X, b, P,
+                                           float(min_dist), idx.ctypes.data, val.ctypes.data, C.byref(n),
+                                           _stream(stream)))
     return idx[:n.value], val[:n.value]
 
 
