@@ -61,6 +61,7 @@ typedef enum {
 
 typedef struct ttm_ctx ttm_ctx;
 typedef struct ttm_plan ttm_plan;
+typedef struct ttm_mlp ttm_mlp;
 
 /* Parameters of the tensor field and of the local normalisation.
  *   order_n          tensor degree n (even; 2, 4 or 6 are built)
@@ -167,9 +168,73 @@ ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream);
  *   d_C       float32 [K][Z][Y][X] (device, from ttm_correlate)
  *   d_score   float32 [Z][Y][X]; d_orient float32 [3][Z][Y][X] (u_x, u_y, u_z)
  *   d_frob    float32 [Z][Y][X] or NULL
- *   mlp       must be NULL for TTM_MAX_PLAIN */
-ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, const void* mlp,
+ *   mode      TTM_MAX_PLAIN: probe directions, multi-start Newton;
+ *             TTM_MAX_MLP_WARM: the MLP's direction (BF16 tensor cores) is
+ *             polished by Newton and kept where the polish converged and
+ *             its value is not below the best of 32 fixed probe directions;
+ *             the other voxels go through the plain maximiser (their count
+ *             is read with ttm_plan_fallback_count). The paper maximises
+ *             with SS-HOPM (Sec. 3.1); the learned start has no counterpart
+ *             there.
+ *   mlp       NULL for TTM_MAX_PLAIN; for TTM_MAX_MLP_WARM an MLP with
+ *             K inputs on the plan's device. The first call after the MLP's
+ *             parameters change rebuilds its BF16 image (synchronous).
+ * The learned mode uses the plan's peak-candidate scratch for its fallback
+ * list: calls on one plan must not overlap. */
+ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, const ttm_mlp* mlp,
                         float* d_score, float* d_orient, float* d_frob, void* stream);
+
+/* Voxels the last TTM_MAX_MLP_WARM ttm_peak_map on this plan handed to the
+ * plain maximiser. Synchronises `stream`. */
+ttm_status ttm_plan_fallback_count(ttm_plan* plan, int64_t* h_count, void* stream);
+
+/* ------------------------------------------- learned warm start (no paper
+ * counterpart): an MLP K -> 128 -> 128 -> 3 with GELU (tanh form) and the
+ * output normalised to a unit vector, trained to predict the maximiser u*
+ * of C . u^{(x)n} from x = C / ||C||_F, loss 1 - (u_hat . u*)^2 (the same
+ * for u* and -u*, as the even form is).
+ * Parameters are one flat FP32 array: W1 [128][K], b1 [128], W2 [128][128],
+ * b2 [128], W3 [3][128], b3 [3] (ttm_mlp_num_params(K) floats). */
+
+/* Number of parameters of the MLP with K inputs (0 if K <= 0). */
+int64_t ttm_mlp_num_params(int n_inputs);
+/* Creates an MLP with n_inputs (1..128) inputs on ctx's device: weights
+ * N(0, 1/fan_in) from a SplitMix64 stream of `seed`, biases 0; Adam state 0.
+ * Allocates parameters, gradients, Adam moments (blocking). */
+ttm_status ttm_mlp_create(ttm_ctx* ctx, int n_inputs, uint64_t seed, ttm_mlp** out);
+void ttm_mlp_destroy(ttm_mlp* mlp);
+int ttm_mlp_inputs(const ttm_mlp* mlp);
+/* Host copy of the parameters (ttm_mlp_num_params floats), blocking. */
+ttm_status ttm_mlp_get_params(const ttm_mlp* mlp, float* h_params);
+/* Sets the parameters from host memory and resets the Adam state. */
+ttm_status ttm_mlp_set_params(ttm_mlp* mlp, const float* h_params);
+/* FP32 forward: d_U [n][3] = u_hat of the rows of d_X [n][K] (device).
+ * Grows the MLP's training scratch on first use (allocates). */
+ttm_status ttm_mlp_forward(ttm_mlp* mlp, const float* d_X, int64_t n, float* d_U, void* stream);
+/* FP32 loss sum over the n rows and its gradient (d_grad, num_params
+ * floats, device) with targets d_U [n][3]; *h_loss on the host
+ * (synchronises). Grows the training scratch on first use. */
+ttm_status ttm_mlp_loss_grad(ttm_mlp* mlp, const float* d_X, const float* d_U, int64_t n,
+                             float* d_grad, double* h_loss, void* stream);
+/* Adam (beta 0.9 / 0.999, eps 1e-8) on the mean loss of minibatches of
+ * `batch` rows, `epochs` passes over a SplitMix64 permutation of the n
+ * pairs per epoch (seeded); whole batches only. *h_last_loss = mean loss of
+ * the last batch of the last epoch. Blocking; allocates its permutation. */
+ttm_status ttm_mlp_train(ttm_mlp* mlp, const float* d_X, const float* d_U, int64_t n, int epochs,
+                         int batch, float lr, uint64_t seed, double* h_last_loss, void* stream);
+/* BF16 tensor-core inference (the arithmetic of the learned maximiser):
+ * d_U [n][3] from d_X [n][K]; K <= 32. */
+ttm_status ttm_mlp_infer(ttm_mlp* mlp, const float* d_X, int64_t n, float* d_U, void* stream);
+/* Training pairs from maps: for each linear voxel index d_idx[i] (device
+ * int64, < V), d_X[i] = C(v) / ||C(v)||_F (zeros where the norm is 0) and
+ * d_U[i] = d_orient(v); C float32 [K][V] of order order_n (d' = 3). */
+ttm_status ttm_mlp_make_pairs(ttm_ctx* ctx, const float* d_C, int order_n, int64_t V,
+                              const float* d_orient, const int64_t* d_idx, int64_t n, float* d_X,
+                              float* d_U, void* stream);
+/* File: 8-byte magic "TTMMLP1", int32 K, int32 128, int64 num_params,
+ * float32 parameters (host byte order). */
+ttm_status ttm_mlp_save(const ttm_mlp* mlp, const char* path);
+ttm_status ttm_mlp_load(ttm_ctx* ctx, const char* path, ttm_mlp** out);
 
 /* --------------------------------------------------------- step a5: Sec. 3.4 */
 

@@ -222,6 +222,8 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
         P->cand_cap = V / 8 + 64;  // strict 26-neighbour maxima are >= 2 apart per axis
         P->cand.alloc(P->cand_cap * (sizeof(int64_t) + sizeof(float)));
         P->cand_count.alloc(sizeof(unsigned long long));
+        P->fb_count.alloc(sizeof(unsigned long long));
+        TTM_CUDA_TRY(cudaMemset(P->fb_count.p, 0, sizeof(unsigned long long)));
         *out = P;
         return TTM_OK;
     } catch (const Error& e) {

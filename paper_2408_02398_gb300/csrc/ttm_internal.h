@@ -83,6 +83,7 @@ struct ttm_plan {
     ttm::DevBuf work;        // float2 [K][Z][Y][Xh]
     ttm::DevBuf cand;        // peak candidates
     ttm::DevBuf cand_count;  // unsigned long long [1]
+    ttm::DevBuf fb_count;    // unsigned long long [1]: learned-maximiser fallbacks of the last call
     int64_t cand_cap = 0;
     // stage timing
     bool timing = false;
@@ -93,7 +94,23 @@ struct ttm_plan {
     ~ttm_plan();
 };
 
+// the warm-start MLP: FP32 parameters with Adam state, training scratch,
+// and the BF16 image used by the tensor-core inference
+struct ttm_mlp {
+    ttm_ctx* ctx = nullptr;
+    int K = 0;
+    int64_t np = 0;
+    int64_t step = 0;
+    ttm::DevBuf params, grad, m, v;
+    int64_t cap = 0;  // rows of training scratch
+    ttm::DevBuf xb, ub, a1, h1, a2, h2, y, dy, loss, part;
+    ttm::DevBuf image;         // kMlpImageBytes, rebuilt when the parameters change
+    bool image_dirty = true;
+};
+
 namespace ttm {
 // set the context error text and return the code
 int fail(ttm_ctx* ctx, const Error& e);
+// rebuild the BF16 inference image if the parameters changed (synchronous)
+void mlp_refresh_image(ttm_mlp* M);
 }

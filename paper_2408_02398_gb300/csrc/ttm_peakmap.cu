@@ -25,6 +25,7 @@
 
 #include <cuda_fp16.h>
 
+#include "mlp_mma.cuh"
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -92,9 +93,10 @@ __device__ __forceinline__ void normalise3(float& x, float& y, float& z)
 }
 
 // up to ITERS polish steps of u towards a local maximum of p; p and A hold
-// the value and contraction at u on entry and on return
+// the value and contraction at u on entry and on return. Returns whether
+// the tangent gradient fell below its tolerance.
 template <int N, int ITERS>
-__device__ void polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p, float* A)
+__device__ bool polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p, float* A)
 {
     const float tol_g2 = 1e-12f * frob * frob;  // |tangent gradient| <= 1e-6 ||C||_F
     const float tol_p = 1e-7f * frob;
@@ -124,7 +126,7 @@ __device__ void polish(const float* c, float frob, float& ux, float& uy, float& 
         const float b1z = (kmax != 2 ? 1.f : 0.f) - r2 * vj2 * vz;
         const float g0 = N * (b0x * ax + b0y * ay + b0z * az);
         const float g1 = N * (b1x * ax + b1y * ay + b1z * az);
-        if (g0 * g0 + g1 * g1 <= tol_g2) break;
+        if (g0 * g0 + g1 * g1 <= tol_g2) return true;
         const float a0x = A[0] * b0x + A[1] * b0y + A[2] * b0z;
         const float a0y = A[1] * b0x + A[3] * b0y + A[4] * b0z;
         const float a0z = A[2] * b0x + A[4] * b0y + A[5] * b0z;
@@ -169,6 +171,7 @@ __device__ void polish(const float* c, float frob, float& ux, float& uy, float& 
             p = form_at<N>(c, ux, uy, uz, A);
         }
     }
+    return false;
 }
 
 // One Newton step (as in polish) for NS starts at once: the starts are
@@ -262,11 +265,21 @@ struct ProbeTables {
     const unsigned char* nbr;  // [kProbes][kProbeNbr] nearest probes (u ~ -u)
 };
 
+// which voxels a k_peakmap launch visits
+enum PmMode { PM_ALL = 0, PM_LIST = 1, PM_SWEEP = 2 };
+
+// PM_ALL: every voxel. PM_LIST: the first min(*list_count, list_cap)
+// entries of list. PM_SWEEP: only if *list_count > list_cap (the list
+// overflowed), every voxel whose score holds the NaN placed there by the
+// learned maximiser.
 template <int N>
 __global__ void __launch_bounds__(kPmThreads)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
-          float* __restrict__ frob, ProbeTables tabs)
+          float* __restrict__ frob, ProbeTables tabs, int mode, const uint32_t* __restrict__ list,
+          const unsigned long long* __restrict__ list_count, int64_t list_cap)
 {
+    if (mode == PM_SWEEP && (int64_t)*list_count <= list_cap) return;
+    const int64_t n_items = mode == PM_LIST ? min((int64_t)*list_count, list_cap) : V;
     constexpr int K = ncomp3(N);
     constexpr int KP = kpad(N);
     constexpr int kStarts = nstarts(N);
@@ -283,9 +296,12 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     }
     __syncthreads();
     // persistent: each CTA walks voxel blocks with a grid stride
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - threadIdx.x < V;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const bool ok = v < V;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t - threadIdx.x < n_items;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = t < n_items;
+        int64_t v = t;
+        if (mode == PM_LIST && ok) v = list[t];
+        if (mode == PM_SWEEP && ok) ok = isnan(score[v]);
         float c[KP];
         float F2 = 0.f;
         {
@@ -389,6 +405,147 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     }
 }
 
+// Learned maximiser: the MLP (BF16 tensor cores) predicts the maximising
+// direction from C / ||C||_F and Newton polishes it. The plain maximiser's
+// probe values (FP32, the same kProbes directions) then serve as the check:
+// where the polished value falls below the best probe, a second polish
+// starts from that probe and the better of the two is kept. A voxel is
+// accepted when its kept polish converged and its value is not below the
+// best probe; the others are appended to `list` (warp-aggregated atomics)
+// for the plain maximiser, and past the list's capacity their score is set
+// to NaN for a sweep instead.
+constexpr int kMlThreads = 256;
+constexpr int kMlWarps = kMlThreads / 32;
+
+template <int N>
+__host__ __device__ constexpr size_t ml_smem_bytes()
+{
+    return kMlpImageBytes + sizeof(__nv_bfloat16) * kMlWarps * 32 * kW1S + sizeof(float) * kMlWarps * 32 * 4 +
+           sizeof(float) * kProbes * kpad(N) + sizeof(float4) * kProbes;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kMlThreads, 2)
+k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
+              float* __restrict__ frob, const unsigned char* __restrict__ image, ProbeTables tabs,
+              uint32_t* __restrict__ list, unsigned long long* __restrict__ count, int64_t cap)
+{
+    constexpr int K = ncomp3(N);
+    constexpr int KP = kpad(N);
+    constexpr int KX = mlp_kx(K);
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* img = smem;
+    size_t off = kMlpImageBytes;
+    __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(smem + off) + (threadIdx.x >> 5) * 32 * kW1S;
+    off += sizeof(__nv_bfloat16) * kMlWarps * 32 * kW1S;
+    float* sy = reinterpret_cast<float*>(smem + off) + (threadIdx.x >> 5) * 32 * 4;
+    off += sizeof(float) * kMlWarps * 32 * 4;
+    float* sphi = reinterpret_cast<float*>(smem + off);
+    off += sizeof(float) * kProbes * KP;
+    float4* sdir = reinterpret_cast<float4*>(smem + off);
+    mlp_image_to_smem(image, img);
+    {
+        const float* phi = N == 2 ? tabs.phi2 : (N == 4 ? tabs.phi4 : tabs.phi6);
+        for (int i = threadIdx.x; i < kProbes * KP; i += blockDim.x) sphi[i] = phi[i];
+        for (int i = threadIdx.x; i < kProbes; i += blockDim.x) sdir[i] = tabs.dir[i];
+    }
+    __syncthreads();
+    const float* b3 = reinterpret_cast<const float*>(img + kMlpOffB3);
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - threadIdx.x < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = v < V;
+        float c[KP];
+        float F2 = 0.f;
+        {
+            int k = 0;
+#pragma unroll
+            for (int a = N; a >= 0; a--)
+#pragma unroll
+                for (int b = N - a; b >= 0; b--) {
+                    const int cc = N - a - b;
+                    const float mult = factf(N) / (factf(a) * factf(b) * factf(cc));
+                    c[k] = ok ? __ldg(C + (int64_t)k * V + v) : 0.f;
+                    F2 += mult * c[k] * c[k];
+                    k++;
+                }
+#pragma unroll
+            for (int k2 = K; k2 < KP; k2++) c[k2] = 0.f;
+        }
+        const float F = sqrtf(F2);
+        const float inv = F > 0.f ? 1.f / F : 0.f;
+        // MLP input row (C / ||C||_F in BF16, zero padded to KX columns)
+#pragma unroll
+        for (int k = 0; k < KX; k += 2) {
+            const float x0 = k < K ? c[k] * inv : 0.f;
+            const float x1 = k + 1 < K ? c[k + 1] * inv : 0.f;
+            *reinterpret_cast<uint32_t*>(sx + lane * kW1S + k) = pack_bf16(x0, x1);
+        }
+        __syncwarp();
+        mlp_warp_bf16<KX>(sx, img, sy);
+        __syncwarp();
+        float ux = sy[lane * 4] + b3[0], uy = sy[lane * 4 + 1] + b3[1], uz = sy[lane * 4 + 2] + b3[2];
+        float best = 0.f;
+        bool accept = true;
+        if (F > 0.f) {
+            const float yn = ux * ux + uy * uy + uz * uz;
+            if (yn > 0.f) normalise3(ux, uy, uz);
+            else { ux = 0.f; uy = 0.f; uz = 1.f; }
+            float A[6];
+            best = form_at<N>(c, ux, uy, uz, A);
+            bool conv = polish<N, kNewtonIters>(c, F, ux, uy, uz, best, A);
+            // best probe, FP32
+            float pm = -INFINITY;
+            int jm = 0;
+#pragma unroll 2
+            for (int j = 0; j < kProbes; j++) {
+                const float4* ph = reinterpret_cast<const float4*>(sphi + j * KP);
+                float pj = 0.f;
+#pragma unroll
+                for (int q = 0; q < KP / 4; q++) {
+                    const float4 f = ph[q];
+                    pj += f.x * c[4 * q] + f.y * c[4 * q + 1] + f.z * c[4 * q + 2] + f.w * c[4 * q + 3];
+                }
+                if (pj > pm) { pm = pj; jm = j; }
+            }
+            const float tol = 1e-5f * F;
+            if (!(conv && best >= pm - tol)) {
+                const float4 d = sdir[jm];
+                float vx = d.x, vy = d.y, vz = d.z, A2[6];
+                float p2 = form_at<N>(c, vx, vy, vz, A2);
+                const bool conv2 = polish<N, kNewtonIters>(c, F, vx, vy, vz, p2, A2);
+                if (p2 > best) { best = p2; ux = vx; uy = vy; uz = vz; conv = conv2; }
+            }
+            accept = conv && best >= pm - tol;
+        } else {
+            ux = 0.f; uy = 0.f; uz = 1.f;
+        }
+        if (uz < 0.f || (uz == 0.f && (uy < 0.f || (uy == 0.f && ux < 0.f)))) { ux = -ux; uy = -uy; uz = -uz; }
+        const bool reject = ok && !accept;
+        const unsigned rmask = __ballot_sync(0xffffffffu, reject);
+        if (rmask) {
+            const int leader = __ffs(rmask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(rmask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (reject) {
+                const unsigned long long pos = base + __popc(rmask & ((1u << lane) - 1u));
+                if ((int64_t)pos < cap) list[pos] = (uint32_t)v;
+                else score[v] = __int_as_float(0x7fc00000);
+            }
+        }
+        if (ok) {
+            if (accept) {
+                score[v] = best;
+                orient[v] = ux;
+                orient[V + v] = uy;
+                orient[2 * V + v] = uz;
+            }
+            if (frob) frob[v] = F;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host --
 
 // probe directions (spherical Fibonacci on the half-sphere z > 0) and the
@@ -457,13 +614,19 @@ void upload_probe_tables(ttm_ctx* ctx)
     for (int i = 0; i < 5; i++) ctx->probe_off[i] = off[i];
 }
 
-void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
-                 cudaStream_t st)
+static ProbeTables probe_tables(ttm_ctx* ctx)
 {
     const float* base = ctx->probe_tables.as<float>();
-    ProbeTables t{reinterpret_cast<const float4*>(base + ctx->probe_off[0]), base + ctx->probe_off[1],
-                  base + ctx->probe_off[2], base + ctx->probe_off[3],
-                  reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4])};
+    return ProbeTables{reinterpret_cast<const float4*>(base + ctx->probe_off[0]), base + ctx->probe_off[1],
+                       base + ctx->probe_off[2], base + ctx->probe_off[3],
+                       reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4])};
+}
+
+// plain maximiser over all voxels (PM_ALL) or the learned path's fallbacks
+static void plain_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
+                      int mode, const uint32_t* list, const unsigned long long* count, int64_t cap, cudaStream_t st)
+{
+    const ProbeTables t = probe_tables(ctx);
     const int64_t blocks = ceil_div(V, kPmThreads);
     const size_t smem = (size_t)kProbes * kPmThreads * sizeof(__half);
     // enough CTAs to fill every SM several times, then a grid stride
@@ -472,7 +635,7 @@ void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, f
     // total, so the dynamic size is always declared
 #define TTM_PM_LAUNCH(N_)                                                                          \
     TTM_CUDA_TRY(cudaFuncSetAttribute(k_peakmap<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k_peakmap<N_><<<(unsigned)grid, kPmThreads, smem, st>>>(C, V, score, orient, frob, t);
+    k_peakmap<N_><<<(unsigned)grid, kPmThreads, smem, st>>>(C, V, score, orient, frob, t, mode, list, count, cap);
     switch (n) {
         case 2: TTM_PM_LAUNCH(2); break;
         case 4: TTM_PM_LAUNCH(4); break;
@@ -483,24 +646,94 @@ void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, f
     TTM_LAUNCH_CHECK();
 }
 
+void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
+                 cudaStream_t st)
+{
+    plain_run(ctx, n, C, V, score, orient, frob, PM_ALL, nullptr, nullptr, 0, st);
+}
+
+// learned maximiser, then the plain one on its rejected voxels
+static void peakmap_learned_run(ttm_plan* P, ttm_mlp* M, const float* C, int64_t V, float* score, float* orient,
+                                float* frob, cudaStream_t st)
+{
+    ttm_ctx* ctx = P->ctx;
+    const int n = P->fp.order_n;
+    uint32_t* list = P->cand.as<uint32_t>();
+    const int64_t cap = (int64_t)(P->cand.bytes / sizeof(uint32_t));
+    unsigned long long* count = P->fb_count.as<unsigned long long>();
+    const ProbeTables tabs = probe_tables(ctx);
+    TTM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    const int64_t blocks = ceil_div(V, kMlThreads);
+    const int64_t grid = std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 2);
+#define TTM_ML_LAUNCH(N_)                                                                                         \
+    {                                                                                                              \
+        const size_t smem = ml_smem_bytes<N_>();                                                                   \
+        TTM_CUDA_TRY(cudaFuncSetAttribute(k_peakmap_mlp<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_peakmap_mlp<N_><<<(unsigned)grid, kMlThreads, smem, st>>>(C, V, score, orient, frob,                     \
+                                                                   M->image.as<unsigned char>(), tabs, list,      \
+                                                                   count, cap);                                   \
+    }
+    switch (n) {
+        case 2: TTM_ML_LAUNCH(2); break;
+        case 4: TTM_ML_LAUNCH(4); break;
+        case 6: TTM_ML_LAUNCH(6); break;
+        default: throw Error{E_UNSUPPORTED, "order must be 2, 4 or 6"};
+    }
+#undef TTM_ML_LAUNCH
+    TTM_LAUNCH_CHECK();
+    plain_run(ctx, n, C, V, score, orient, frob, PM_LIST, list, count, cap, st);
+    plain_run(ctx, n, C, V, score, orient, frob, PM_SWEEP, list, count, cap, st);
+}
+
 }  // namespace ttm
 
 using namespace ttm;
 
-extern "C" ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, const void* mlp,
+extern "C" ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximiser mode, const ttm_mlp* mlp,
                                    float* d_score, float* d_orient, float* d_frob, void* stream)
 {
     if (!plan) return TTM_E_INVALID_ARG;
     try {
         TTM_REQUIRE(d_C && d_score && d_orient, E_INVALID_ARG, "null pointer argument");
-        TTM_REQUIRE(mode == TTM_MAX_PLAIN, E_UNSUPPORTED, "only the plain maximiser is built in this version");
-        TTM_REQUIRE(mlp == nullptr, E_INVALID_ARG, "mlp must be NULL for the plain maximiser");
+        TTM_REQUIRE(mode == TTM_MAX_PLAIN || mode == TTM_MAX_MLP_WARM, E_INVALID_ARG, "unknown maximiser");
+        TTM_REQUIRE(mode == TTM_MAX_MLP_WARM || mlp == nullptr, E_INVALID_ARG,
+                    "mlp must be NULL for the plain maximiser");
+        TTM_REQUIRE(mode == TTM_MAX_PLAIN || mlp != nullptr, E_INVALID_ARG, "the learned maximiser needs an mlp");
+        TTM_REQUIRE(plan->fp.dprime == 3, E_UNSUPPORTED, "the GPU maximiser works on the 2-sphere (d' = 3)");
         TTM_CUDA_TRY(cudaSetDevice(plan->ctx->device));
         const Prep& p = plan->prep;
         const int64_t V = (int64_t)p.Z * p.Y * p.X;
-        stage_begin(plan, (cudaStream_t)stream);
-        peakmap_run(plan->ctx, plan->fp.order_n, d_C, V, d_score, d_orient, d_frob, (cudaStream_t)stream);
-        stage_end(plan, ST_PEAKMAP, (cudaStream_t)stream);
+        cudaStream_t st = (cudaStream_t)stream;
+        if (mode == TTM_MAX_MLP_WARM) {
+            ttm_mlp* M = const_cast<ttm_mlp*>(mlp);
+            TTM_REQUIRE(M->K == plan->K, E_INVALID_ARG, "mlp input count differs from the plan's component count");
+            TTM_REQUIRE(M->ctx->device == plan->ctx->device, E_INVALID_ARG, "mlp lives on another device");
+            TTM_REQUIRE(V <= (int64_t)UINT32_MAX, E_SHAPE, "the learned maximiser indexes voxels with 32 bits");
+            mlp_refresh_image(M);
+            stage_begin(plan, st);
+            peakmap_learned_run(plan, M, d_C, V, d_score, d_orient, d_frob, st);
+            stage_end(plan, ST_PEAKMAP, st);
+        } else {
+            stage_begin(plan, st);
+            peakmap_run(plan->ctx, plan->fp.order_n, d_C, V, d_score, d_orient, d_frob, st);
+            stage_end(plan, ST_PEAKMAP, st);
+        }
+        return TTM_OK;
+    } catch (const Error& e) {
+        return (ttm_status)fail(plan->ctx, e);
+    }
+}
+
+extern "C" ttm_status ttm_plan_fallback_count(ttm_plan* plan, int64_t* h_count, void* stream)
+{
+    if (!plan || !h_count) return TTM_E_INVALID_ARG;
+    try {
+        TTM_CUDA_TRY(cudaSetDevice(plan->ctx->device));
+        unsigned long long n = 0;
+        cudaStream_t st = (cudaStream_t)stream;
+        TTM_CUDA_TRY(cudaMemcpyAsync(&n, plan->fb_count.p, sizeof(n), cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        *h_count = (int64_t)n;
         return TTM_OK;
     } catch (const Error& e) {
         return (ttm_status)fail(plan->ctx, e);

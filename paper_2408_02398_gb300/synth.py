@@ -240,22 +240,31 @@ def make_workload(shape, n_tmpl: int, mask_radius: float, order_n: int, copies: 
     with `copies` planted templates at uniform random rotations. Give either a
     fixed amplitude (template max = 1) or an SNR = in-mask variance of the
     scaled template / noise variance."""
+    tmpl = gaussian_blob_template(n_tmpl, seed, index=template_index)
+    vol, planted = make_tomogram(shape, tmpl, mask_radius, copies, seed, amplitude=amplitude, snr=snr,
+                                 lowpass=lowpass)
+    return Workload(tomo=vol, template=tmpl.astype(np.float32), mask_radius=mask_radius, order_n=order_n,
+                    planted=planted, name=name)
+
+
+def make_tomogram(shape, tmpl: np.ndarray, mask_radius: float, copies: int, seed: int,
+                  amplitude: float | None = None, snr: float | None = None, lowpass: bool = False):
+    """Noise tomogram with `copies` planted copies of a given template (see
+    make_workload); returns (float32 volume, Planted)."""
     Z, Y, X = shape
+    n_tmpl = tmpl.shape[0]
     noise = normals(seed, STREAM_NOISE, Z * Y * X).reshape(Z, Y, X)
     if lowpass:
         noise = lowpass_gaussian_periodic(noise)
         noise /= noise.std()
-    tmpl = gaussian_blob_template(n_tmpl, seed, index=template_index)
     if amplitude is None:
         m = sphere_mask_values(n_tmpl, mask_radius)
-        amplitude = math.sqrt(float(snr) / float(np.var(tmpl[m])))
+        amplitude = math.sqrt(float(snr) / float(np.var(np.asarray(tmpl, dtype=np.float64)[m])))
     centres = place_centres(shape, n_tmpl, copies, 2.0 * mask_radius, seed)
     quats = shoemake_quats(uniforms(seed, STREAM_ROT, 3 * len(centres)))
     vol = noise
-    plant(vol, tmpl, centres, quats, amplitude)
-    return Workload(tomo=vol.astype(np.float32), template=tmpl.astype(np.float32),
-                    mask_radius=mask_radius, order_n=order_n,
-                    planted=Planted(centres, quats, amplitude), name=name)
+    plant(vol, np.asarray(tmpl, dtype=np.float64), centres, quats, amplitude)
+    return vol.astype(np.float32), Planted(centres, quats, amplitude)
 
 
 # ---------------------------------------------------------------------------

@@ -29,7 +29,10 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_
            "ttm_plan_components", "ttm_plan_valid_box", "ttm_correlate", "ttm_plan_copy_w", "ttm_peak_map",
            "ttm_find_peaks", "tm_correlate", "ttm_plan_enable_timing", "ttm_plan_stage_times", "ttm_num_stages",
            "ttm_stage_name", "ttm_kernel_launches", "ttm_plan_set_localsum",
-           "ttm_find_peaks_noalloc"]
+           "ttm_find_peaks_noalloc", "ttm_plan_fallback_count", "ttm_mlp_num_params", "ttm_mlp_create",
+           "ttm_mlp_destroy", "ttm_mlp_inputs", "ttm_mlp_get_params", "ttm_mlp_set_params", "ttm_mlp_forward",
+           "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
+           "ttm_mlp_load"]
 
 
 class TTMError(RuntimeError):
@@ -84,6 +87,20 @@ def lib():
             "ttm_kernel_launches": (C.c_uint64, []),
             "ttm_plan_set_localsum": (_i, [_vp, _i]),
             "ttm_find_peaks_noalloc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _d, _vp, _vp, C.POINTER(_i), _vp]),
+            "ttm_plan_fallback_count": (_i, [_vp, C.POINTER(_i64), _vp]),
+            "ttm_mlp_num_params": (_i64, [_i]),
+            "ttm_mlp_create": (_i, [_vp, _i, C.c_uint64, C.POINTER(_vp)]),
+            "ttm_mlp_destroy": (None, [_vp]),
+            "ttm_mlp_inputs": (_i, [_vp]),
+            "ttm_mlp_get_params": (_i, [_vp, _vp]),
+            "ttm_mlp_set_params": (_i, [_vp, _vp]),
+            "ttm_mlp_forward": (_i, [_vp, _vp, _i64, _vp, _vp]),
+            "ttm_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i64, _vp, C.POINTER(_d), _vp]),
+            "ttm_mlp_train": (_i, [_vp, _vp, _vp, _i64, _i, _i, C.c_float, C.c_uint64, C.POINTER(_d), _vp]),
+            "ttm_mlp_infer": (_i, [_vp, _vp, _i64, _vp, _vp]),
+            "ttm_mlp_make_pairs": (_i, [_vp, _vp, _i, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+            "ttm_mlp_save": (_i, [_vp, C.c_char_p]),
+            "ttm_mlp_load": (_i, [_vp, C.c_char_p, C.POINTER(_vp)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,11 +247,101 @@ def ttm_plan_copy_w(plan: Plan, d_w, stream=None):
 
 def ttm_peak_map(plan: Plan, d_C, d_score, d_orient, d_frob=None, mode=TTM_MAX_PLAIN, mlp=None, stream=None):
     import torch
-    plan.ctx.check(lib().ttm_peak_map(plan.h, _dev(d_C, torch.float32, "d_C"), mode, mlp,
+    if mlp is not None and mode == TTM_MAX_PLAIN:
+        mode = TTM_MAX_MLP_WARM
+    plan.ctx.check(lib().ttm_peak_map(plan.h, _dev(d_C, torch.float32, "d_C"), mode,
+                                      None if mlp is None else mlp.h,
                                       _dev(d_score, torch.float32, "d_score"),
                                       _dev(d_orient, torch.float32, "d_orient"),
                                       None if d_frob is None else _dev(d_frob, torch.float32, "d_frob"),
                                       _stream(stream)))
+
+
+def ttm_plan_fallback_count(plan: Plan, stream=None) -> int:
+    n = C.c_int64(0)
+    plan.ctx.check(lib().ttm_plan_fallback_count(plan.h, C.byref(n), _stream(stream)))
+    return n.value
+
+
+# ------------------------------------------------------ learned warm start --
+
+def ttm_mlp_num_params(n_inputs: int) -> int:
+    return lib().ttm_mlp_num_params(n_inputs)
+
+
+class Mlp:
+    """ttm_mlp: the warm-start network K -> 128 -> 128 -> 3 on one device."""
+
+    def __init__(self, ctx: Context, n_inputs: int = 0, seed: int = 0, handle=None):
+        self.ctx = ctx
+        if handle is None:
+            h = _vp()
+            ctx.check(lib().ttm_mlp_create(ctx.h, n_inputs, seed, C.byref(h)))
+            handle = h
+        self.h = handle
+        self.K = lib().ttm_mlp_inputs(self.h)
+        self.num_params = lib().ttm_mlp_num_params(self.K)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ttm_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.num_params, dtype=np.float32)
+        self.ctx.check(lib().ttm_mlp_get_params(self.h, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        self.ctx.check(lib().ttm_mlp_set_params(self.h, p.ctypes.data))
+
+    def forward(self, d_X, d_U, stream=None):
+        import torch
+        self.ctx.check(lib().ttm_mlp_forward(self.h, _dev(d_X, torch.float32, "d_X"), d_X.shape[0],
+                                             _dev(d_U, torch.float32, "d_U"), _stream(stream)))
+
+    def infer(self, d_X, d_U, stream=None):
+        import torch
+        self.ctx.check(lib().ttm_mlp_infer(self.h, _dev(d_X, torch.float32, "d_X"), d_X.shape[0],
+                                           _dev(d_U, torch.float32, "d_U"), _stream(stream)))
+
+    def loss_grad(self, d_X, d_U, d_grad, stream=None) -> float:
+        import torch
+        L = C.c_double(0)
+        self.ctx.check(lib().ttm_mlp_loss_grad(self.h, _dev(d_X, torch.float32, "d_X"),
+                                               _dev(d_U, torch.float32, "d_U"), d_X.shape[0],
+                                               _dev(d_grad, torch.float32, "d_grad"), C.byref(L), _stream(stream)))
+        return L.value
+
+    def train(self, d_X, d_U, epochs=20, batch=4096, lr=1e-3, seed=0, stream=None) -> float:
+        import torch
+        L = C.c_double(0)
+        self.ctx.check(lib().ttm_mlp_train(self.h, _dev(d_X, torch.float32, "d_X"),
+                                           _dev(d_U, torch.float32, "d_U"), d_X.shape[0], epochs, batch,
+                                           float(lr), seed, C.byref(L), _stream(stream)))
+        return L.value
+
+    def save(self, path: str):
+        self.ctx.check(lib().ttm_mlp_save(self.h, path.encode()))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Mlp":
+        h = _vp()
+        ctx.check(lib().ttm_mlp_load(ctx.h, path.encode(), C.byref(h)))
+        return cls(ctx, handle=h)
+
+
+def ttm_mlp_make_pairs(ctx: Context, d_C, order_n: int, d_orient, d_idx, d_X, d_U, stream=None):
+    import torch
+    V = d_C[0].numel()
+    ctx.check(lib().ttm_mlp_make_pairs(ctx.h, _dev(d_C, torch.float32, "d_C"), order_n, V,
+                                       _dev(d_orient, torch.float32, "d_orient"), _dev(d_idx, torch.int64, "d_idx"),
+                                       d_idx.shape[0], _dev(d_X, torch.float32, "d_X"),
+                                       _dev(d_U, torch.float32, "d_U"), _stream(stream)))
 
 
 def ttm_find_peaks(plan: Plan, d_map, P: int, min_dist: float, stream=None):
@@ -309,7 +416,7 @@ class Matcher:
         self.orient = torch.empty((3, Z, Y, X), dtype=torch.float32, device=device)
         self.frob = torch.empty((Z, Y, X), dtype=torch.float32, device=device)
 
-    def run(self, d_tomo, stream=None):
+    def run(self, d_tomo, stream=None, mlp=None):
         ttm_correlate(self.plan, d_tomo, self.C, stream)
-        ttm_peak_map(self.plan, self.C, self.score, self.orient, self.frob, stream=stream)
+        ttm_peak_map(self.plan, self.C, self.score, self.orient, self.frob, mlp=mlp, stream=stream)
         return self.score, self.orient, self.frob
