@@ -126,7 +126,17 @@ ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, int tz, int
 /* A plan binds a tensor field to one tomogram shape: it holds the template
  * spectra (transformed along x and y, kept on the template's z rows), the
  * spectrum of the mask, and the per-tomogram workspace. Allocates device
- * memory (~ (K + 6) * Z*Y*(X/2+1) * 8 bytes for FP32). Blocking. */
+ * memory (~ (K + 6) * Z*Y*(X/2+1) * 8 bytes for FP32). Blocking.
+ *   precision  TTM_PREC_FP32, or TTM_PREC_FP16_SPECTRA / _BF16_SPECTRA:
+ *              the template spectra and the K-component work buffer are
+ *              stored as 16-bit pairs (half the bytes), each component
+ *              scaled by 1 / max |its partial spectrum|, the image spectrum
+ *              divided by its largest modulus, and the z- and y-pass stores
+ *              scaled by fixed factors that keep the a-priori bounds
+ *              (Z tz, then Z tz Y) below 2^15; all transform arithmetic and
+ *              the output C stay FP32, the local variance FP64. Expected
+ *              error of C: about one unit roundoff (2^-11 FP16, 2^-8 BF16)
+ *              relative, at most three. */
 ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
                            const ttm_field_params* params, int Z, int Y, int X,
                            ttm_precision precision, ttm_plan** out);

@@ -14,10 +14,24 @@
 // DIR = +1 the unnormalised inverse.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ttm_common.cuh"
 #include "df64.cuh"
 
 namespace ttm {
+
+// Complex values as stored in HBM: the pass precision itself, or FP16 /
+// BF16 pairs that are widened to FP32 on load (the arithmetic stays FP32).
+__device__ __forceinline__ float2 load_cx(const float2& v) { return v; }
+__device__ __forceinline__ double2 load_cx(const double2& v) { return v; }
+__device__ __forceinline__ dcx load_cx(const dcx& v) { return v; }
+__device__ __forceinline__ float2 load_cx(const __half2& v) { return __half22float2(v); }
+__device__ __forceinline__ float2 load_cx(const __nv_bfloat162& v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ void store_cx(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void store_cx(__half2* p, float2 v) { *p = __float22half2_rn(v); }
+__device__ __forceinline__ void store_cx(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
 constexpr int kMaxStages = 24;
 
@@ -223,8 +237,8 @@ struct StridedAxis {
 // ------------------------------------------------------------ kernels --
 
 // Shared memory: 2 * W * ld + L complex elements.
-template <typename R, int DIR, class Pro, class Store>
-__global__ void __launch_bounds__(256) k_fft_strided(const cx<R>* __restrict__ in, StridedAxis ax, LenPlan pl,
+template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
+__global__ void __launch_bounds__(256) k_fft_strided(const In* __restrict__ in, StridedAxis ax, LenPlan pl,
                                                      int W, int ld, Pro pro, Store store)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -240,7 +254,7 @@ __global__ void __launch_bounds__(256) k_fft_strided(const cx<R>* __restrict__ i
         int j = idx / W, w = idx - j * W;
         int64_t i = i0 + w;
         cx<R> v = mk<R>(0, 0);
-        if (i < ax.inner) v = pro(in[o * ax.os + i + (int64_t)j * ax.s], o, i, j);
+        if (i < ax.inner) v = pro(load_cx(in[o * ax.os + i + (int64_t)j * ax.s]), o, i, j);
         bufa[w * ld + j] = v;
     }
     __syncthreads();
@@ -326,8 +340,8 @@ __global__ void __launch_bounds__(256) k_r2c_rows(Src src, int64_t nrows, cx<R>*
 // IFFT(Z) = a + i b. `sink(row, x, value)` consumes the real outputs
 // (normalisation / max epilogues). `in` may be offset per blockIdx.y by
 // in_batch_stride for batched use; the sink gets blockIdx.y via `batch`.
-template <typename R, class Sink>
-__global__ void __launch_bounds__(256) k_c2r_rows(const cx<R>* __restrict__ in, int64_t nrows, Sink sink,
+template <typename R, class Sink, typename In = cx<R>>
+__global__ void __launch_bounds__(256) k_c2r_rows(const In* __restrict__ in, int64_t nrows, Sink sink,
                                                   LenPlan pl, int W, int ld, int nbatch)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -340,13 +354,13 @@ __global__ void __launch_bounds__(256) k_c2r_rows(const cx<R>* __restrict__ in, 
     const int batch = blockIdx.x % nbatch;
     const int64_t tile = blockIdx.x / nbatch;
     const int64_t r0 = tile * 2 * W;
-    const cx<R>* src = in + (int64_t)batch * nrows * Xh;
+    const In* src = in + (int64_t)batch * nrows * Xh;
     load_twiddles<R>(tws, pl);
     for (int idx = threadIdx.x; idx < W * Xh; idx += blockDim.x) {
         int w = idx / Xh, k = idx - w * Xh;
         int64_t ra = r0 + 2 * w, rb = ra + 1;
-        cx<R> A = ra < nrows ? src[ra * Xh + k] : mk<R>(0, 0);
-        cx<R> B = rb < nrows ? src[rb * Xh + k] : mk<R>(0, 0);
+        cx<R> A = ra < nrows ? load_cx(src[ra * Xh + k]) : mk<R>(0, 0);
+        cx<R> B = rb < nrows ? load_cx(src[rb * Xh + k]) : mk<R>(0, 0);
         if (k == 0 || (2 * k == X)) { A.y = 0; B.y = 0; }
         // Z(k) = A + iB
         bufa[w * ld + k] = mk<R>(A.x - B.y, A.y + B.x);
@@ -408,12 +422,12 @@ inline void set_smem(K kernel, size_t bytes)
 }
 
 // strided-axis pass (lines adjacent along the inner index)
-template <typename R, int DIR, class Pro, class Store>
-inline void launch_strided(const cx<R>* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
+template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
+inline void launch_strided(const In* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
                            cudaStream_t st)
 {
     TileShape ts = choose_tile(pl.L, sizeof(cx<R>), 4, 16);
-    auto k = k_fft_strided<R, DIR, Pro, Store>;
+    auto k = k_fft_strided<R, DIR, Pro, Store, In>;
     set_smem(k, ts.smem);
     int64_t grid = ax.outer * ceil_div(ax.inner, ts.W);
     TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "strided pass grid too large");
@@ -444,12 +458,12 @@ inline void launch_r2c_rows(Src src, int64_t nrows, cx<R>* out, const LenPlan& p
     TTM_LAUNCH_CHECK();
 }
 
-template <typename R, class Sink>
-inline void launch_c2r_rows(const cx<R>* in, int64_t nrows, Sink sink, const LenPlan& pl, int nbatch,
+template <typename R, class Sink, typename In = cx<R>>
+inline void launch_c2r_rows(const In* in, int64_t nrows, Sink sink, const LenPlan& pl, int nbatch,
                             cudaStream_t st)
 {
     TileShape ts = choose_tile(pl.L, sizeof(cx<R>), 1, 8);
-    auto k = k_c2r_rows<R, Sink>;
+    auto k = k_c2r_rows<R, Sink, In>;
     set_smem(k, ts.smem);
     int64_t grid = ceil_div(nrows, 2 * ts.W) * nbatch;
     TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "c2r pass grid too large");

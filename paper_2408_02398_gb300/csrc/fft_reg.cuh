@@ -110,9 +110,9 @@ __device__ __forceinline__ void fs_phase1(cx<R>* x, int p, cx<R>* xch, const cx<
 
 // strided axis: lines (o, i), i adjacent (w fastest in the CTA), elements
 // at o*os + i + j*s. Natural order in and out.
-template <typename R, int E, int P, int DIR, class Pro, class Store>
+template <typename R, int E, int P, int DIR, class Pro, class Store, typename In = cx<R>>
 __global__ void __launch_bounds__(FsThreads<R>::value)
-k_fs_strided(const cx<R>* __restrict__ in, StridedAxis ax, const void* twg, Pro pro, Store store)
+k_fs_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro pro, Store store)
 {
     using S = FsShape<R, E, P>;
     extern __shared__ unsigned char smem_raw[];
@@ -126,11 +126,11 @@ k_fs_strided(const cx<R>* __restrict__ in, StridedAxis ax, const void* twg, Pro 
     const bool act = i < ax.inner;
     fs_load_tw<R>(tw, twg, S::L);
     cx<R> x[E];
-    const cx<R>* src = in + o * ax.os + i;
+    const In* src = in + o * ax.os + i;
 #pragma unroll
     for (int m = 0; m < E; m++) {
         const int j = p + P * m;
-        x[m] = act ? pro(src[(int64_t)j * ax.s], o, i, j) : mk<R>(0, 0);
+        x[m] = act ? pro(load_cx(src[(int64_t)j * ax.s]), o, i, j) : mk<R>(0, 0);
     }
     __syncthreads();
     fs_phase1<R, E, P, DIR>(x, p, xa + w * S::LD, tw);
@@ -241,9 +241,9 @@ k_fs_r2c(Src src, int64_t nrows, cx<R>* __restrict__ out, const void* twg)
 
 // inverse complex-to-real rows (2-for-1, see k_c2r_rows), batched: the
 // component index is the fastest grid index.
-template <typename R, int E, int P, class Sink>
+template <typename R, int E, int P, class Sink, typename In = cx<R>>
 __global__ void __launch_bounds__(FsThreads<R>::value)
-k_fs_c2r(const cx<R>* __restrict__ in, int64_t nrows, Sink sink, const void* twg, int nbatch)
+k_fs_c2r(const In* __restrict__ in, int64_t nrows, Sink sink, const void* twg, int nbatch)
 {
     using S = FsShape<R, E, P>;
     constexpr int X = S::L, Xh = X / 2 + 1;
@@ -255,8 +255,8 @@ k_fs_c2r(const cx<R>* __restrict__ in, int64_t nrows, Sink sink, const void* twg
     const int batch = blockIdx.x % nbatch;
     const int64_t tile = blockIdx.x / nbatch;
     const int64_t ra = tile * 2 * S::W + 2 * w, rb = ra + 1;
-    const cx<R>* ba = in + ((int64_t)batch * nrows + ra) * Xh;
-    const cx<R>* bb = ba + Xh;
+    const In* ba = in + ((int64_t)batch * nrows + ra) * Xh;
+    const In* bb = ba + Xh;
     const bool va = ra < nrows, vb = rb < nrows;
     fs_load_tw<R>(tw, twg, S::L);
     cx<R> x[E];
@@ -264,8 +264,8 @@ k_fs_c2r(const cx<R>* __restrict__ in, int64_t nrows, Sink sink, const void* twg
     for (int m = 0; m < E; m++) {
         const int k = p + P * m;
         const int kk = k < Xh ? k : X - k;
-        cx<R> A = va ? ba[kk] : mk<R>(0, 0);
-        cx<R> B = vb ? bb[kk] : mk<R>(0, 0);
+        cx<R> A = va ? load_cx(ba[kk]) : mk<R>(0, 0);
+        cx<R> B = vb ? load_cx(bb[kk]) : mk<R>(0, 0);
         if (kk == 0 || 2 * kk == X) { A.y = 0; B.y = 0; }
         // Z(k) = A + iB below X/2, conj A + i conj B above
         x[m] = k < Xh ? mk<R>(A.x - B.y, A.y + B.x) : mk<R>(A.x + B.y, -A.y + B.x);
@@ -293,10 +293,13 @@ k_fs_c2r(const cx<R>* __restrict__ in, int64_t nrows, Sink sink, const void* twg
 // forward four-step of the template column, product with the image
 // spectrum in the (k1 + E k2) layout (held in registers for all K), and the
 // inverse four-step run backwards to the natural layout.
-template <int E, int P>
+// TS / TW: storage of the template spectra and of the output (float2, or
+// FP16 / BF16 pairs); gmax (or NULL): the image spectrum is multiplied by
+// 1 / *gmax as it is loaded, so that scaled products stay in FP16 range.
+template <int E, int P, typename TS = float2, typename TW = float2>
 __global__ void __launch_bounds__(FsThreads<float>::value, 2)
-k_fs_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
-           float2* __restrict__ out, const void* twg)
+k_fs_zcorr(const float2* __restrict__ G, const TS* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
+           TW* __restrict__ out, const void* twg, const float* __restrict__ gmax, float oscale)
 {
     using S = FsShape<float, E, P>;
     constexpr int Z = S::L;
@@ -312,23 +315,24 @@ k_fs_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K,
     // image-spectrum tile, loaded once for all K components (coalesced: the
     // W columns of a row are adjacent)
     float2* gsm = xa + S::W * S::LD;
+    const float gs = (gmax && *gmax > 0.f) ? 1.f / *gmax : 1.f;
     for (int idx = t; idx < S::W * Z; idx += blockDim.x) {
         const int z = idx / S::W, ww = idx - z * S::W;
         const int64_t cc = (int64_t)blockIdx.x * S::W + ww;
-        gsm[ww * ZG + z] = cc < ncols ? G[(int64_t)z * ncols + cc] : make_float2(0.f, 0.f);
+        gsm[ww * ZG + z] = cc < ncols ? cscale(G[(int64_t)z * ncols + cc], gs) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const float2* gl = gsm + w * ZG;
     float2* xl = xa + w * S::LD;
     for (int a = 0; a < K; a++) {
-        const float2* sp = spec + (int64_t)a * tzn * ncols;
+        const TS* sp = spec + (int64_t)a * tzn * ncols;
         float2 x[E];
 #pragma unroll
         for (int m = 0; m < E; m++) {
             // template row j lands on z = (j - cz) mod Z
             int j = p + P * m + cz;
             if (j >= Z) j -= Z;
-            x[m] = (act && j < tzn) ? sp[(int64_t)j * ncols + c] : make_float2(0.f, 0.f);
+            x[m] = (act && j < tzn) ? load_cx(sp[(int64_t)j * ncols + c]) : make_float2(0.f, 0.f);
         }
         fs_phase1<float, E, P, -1>(x, p, xl, tw);
         __syncthreads();
@@ -358,9 +362,9 @@ k_fs_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K,
         for (int k1 = 0; k1 < E; k1++) x[k1] = xl[k1 * S::KS + p];
         dft_reg<E, +1, S::L, float>(x, tw);
         if (act) {
-            float2* o = out + (int64_t)a * Z * ncols + c;
+            TW* o = out + (int64_t)a * Z * ncols + c;
 #pragma unroll
-            for (int m = 0; m < E; m++) o[(int64_t)(p + P * m) * ncols] = x[m];
+            for (int m = 0; m < E; m++) store_cx(o + (int64_t)(p + P * m) * ncols, cscale(x[m], oscale));
         }
         __syncthreads();  // all reads of xl done before the next component writes it
     }
@@ -393,8 +397,8 @@ inline bool fs_split(int L, int& E, int& P)
         default: throw Error{E_INTERNAL, "no register FFT for this length"}; \
     }
 
-template <typename R, int DIR, class Pro, class Store>
-inline void launch_strided_any(const cx<R>* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
+template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
+inline void launch_strided_any(const In* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
                                cudaStream_t st)
 {
     int E, P;
@@ -402,7 +406,7 @@ inline void launch_strided_any(const cx<R>* in, StridedAxis ax, const LenPlan& p
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \
-        auto k = k_fs_strided<R, E_, P_, DIR, Pro, Store>;                                     \
+        auto k = k_fs_strided<R, E_, P_, DIR, Pro, Store, In>;                                   \
         set_smem(k, S::SMEM);                                                                  \
         int64_t grid = ax.outer * ceil_div(ax.inner, S::W);                                    \
         TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "strided pass grid too large");               \
@@ -448,8 +452,9 @@ inline void launch_r2c_any(Src src, int64_t nrows, cx<R>* out, const LenPlan& pl
     TTM_LAUNCH_CHECK();
 }
 
-inline bool launch_zcorr_fs(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols,
-                            float2* out, const LenPlan& pz, cudaStream_t st)
+template <typename TS, typename TW>
+inline bool launch_zcorr_fs(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
+                            const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st)
 {
     int E, P;
     if (!fs_split(pz.L, E, P)) return false;
@@ -457,9 +462,9 @@ inline bool launch_zcorr_fs(const float2* G, const float2* spec, int K, int tzn,
     {                                                                                          \
         using S = FsShape<float, E_, P_>;                                                      \
         const size_t smem = S::SMEM + (size_t)S::W * (S::L | 1) * sizeof(float2);              \
-        auto k = k_fs_zcorr<E_, P_>;                                                           \
+        auto k = k_fs_zcorr<E_, P_, TS, TW>;                                                   \
         set_smem(k, smem);                                                                     \
-        k<<<(unsigned)ceil_div(ncols, S::W), S::THREADS, smem, st>>>(G, spec, K, tzn, cz, ncols, out, pz.tw); \
+        k<<<(unsigned)ceil_div(ncols, S::W), S::THREADS, smem, st>>>(G, spec, K, tzn, cz, ncols, out, pz.tw, gmax, oscale); \
     }
     TTM_FS_SWITCH(pz.L, TTM_L)
 #undef TTM_L
@@ -467,8 +472,8 @@ inline bool launch_zcorr_fs(const float2* G, const float2* spec, int K, int tzn,
     return true;
 }
 
-template <typename R, class Sink>
-inline void launch_c2r_any(const cx<R>* in, int64_t nrows, Sink sink, const LenPlan& pl, int nbatch,
+template <typename R, class Sink, typename In = cx<R>>
+inline void launch_c2r_any(const In* in, int64_t nrows, Sink sink, const LenPlan& pl, int nbatch,
                            cudaStream_t st)
 {
     int E, P;
@@ -476,7 +481,7 @@ inline void launch_c2r_any(const cx<R>* in, int64_t nrows, Sink sink, const LenP
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \
-        auto k = k_fs_c2r<R, E_, P_, Sink>;                                                    \
+        auto k = k_fs_c2r<R, E_, P_, Sink, In>;                                                 \
         set_smem(k, S::SMEM);                                                                  \
         int64_t grid = ceil_div(nrows, 2 * S::W) * nbatch;                                     \
         TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "c2r pass grid too large");                   \

@@ -11,6 +11,7 @@
 // and transforms back along z. Then a y pass over all K components and an
 // x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
 
+#include <algorithm>
 #include <vector>
 
 #include "fft_reg.cuh"
@@ -43,9 +44,10 @@ __global__ void k_spec_store(const double2* __restrict__ src, int64_t n, double 
 // Fused z pass. Columns c in [0, ncols) (ncols = Y * Xh) are the (ky, kx)
 // pairs; element z of column c is at z * ncols + c. One CTA owns W adjacent
 // columns. Shared memory: 3 * W * ld + Z complex.
+template <typename TS, typename TW>
 __global__ void __launch_bounds__(256)
-k_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
-        float2* __restrict__ out, LenPlan pl, int W, int ld)
+k_zcorr(const float2* __restrict__ G, const TS* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
+        TW* __restrict__ out, LenPlan pl, int W, int ld, const float* __restrict__ gmax, float oscale)
 {
     extern __shared__ unsigned char smem_raw[];
     float2* gs = reinterpret_cast<float2*>(smem_raw);
@@ -55,23 +57,24 @@ k_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K, in
     const int Z = pl.L;
     const int64_t c0 = (int64_t)blockIdx.x * W;
     load_twiddles<float>(tws, pl);
+    const float gsc = (gmax && *gmax > 0.f) ? 1.f / *gmax : 1.f;
     for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
         int z = idx / W, w = idx - z * W;
         int64_t c = c0 + w;
-        gs[w * ld + z] = c < ncols ? G[(int64_t)z * ncols + c] : make_float2(0.f, 0.f);
+        gs[w * ld + z] = c < ncols ? cscale(G[(int64_t)z * ncols + c], gsc) : make_float2(0.f, 0.f);
     }
     const int64_t comp_stride = (int64_t)tzn * ncols;
     const int64_t out_stride = (int64_t)Z * ncols;
     for (int a = 0; a < K; a++) {
         // template rows j land on z = (j - cz) mod Z, i.e. j = (z + cz) mod Z
-        const float2* sp = spec + a * comp_stride;
+        const TS* sp = spec + a * comp_stride;
         for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
             int z = idx / W, w = idx - z * W;
             int64_t c = c0 + w;
             int j = z + cz;
             if (j >= Z) j -= Z;
             float2 v = make_float2(0.f, 0.f);
-            if (j < tzn && c < ncols) v = sp[(int64_t)j * ncols + c];
+            if (j < tzn && c < ncols) v = load_cx(sp[(int64_t)j * ncols + c]);
             bufa[w * ld + z] = v;
         }
         __syncthreads();
@@ -83,11 +86,11 @@ k_zcorr(const float2* __restrict__ G, const float2* __restrict__ spec, int K, in
         }
         __syncthreads();
         float2* r = smem_fft<+1, float>(p, q, ld, W, pl, tws);
-        float2* o = out + a * out_stride;
+        TW* o = out + a * out_stride;
         for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
             int z = idx / W, w = idx - z * W;
             int64_t c = c0 + w;
-            if (c < ncols) o[(int64_t)z * ncols + c] = r[w * ld + z];
+            if (c < ncols) store_cx(o + (int64_t)z * ncols + c, cscale(r[w * ld + z], oscale));
         }
         __syncthreads();
     }
@@ -108,20 +111,94 @@ struct SinkNormalise {
     }
 };
 
-void launch_zcorr(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
-                  const LenPlan& pz, cudaStream_t st)
+// ------------------------------------------- 16-bit spectra (FP16 / BF16)
+
+template <typename T16>
+__global__ void k_spec_store16(const double2* __restrict__ src, int64_t n, double scale, T16* __restrict__ dst)
 {
-    if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, st)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = src[i];
+        store_cx(dst + i, make_float2((float)(v.x * scale), (float)(v.y * scale)));
+    }
+}
+
+// per-block max |v| of a double2 array (host finishes the reduction)
+__global__ void k_maxabs_d2(const double2* __restrict__ v, int64_t n, double* __restrict__ part)
+{
+    __shared__ double s[256];
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, hypot(v[i].x, v[i].y));
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// *out = max |G| (out zeroed first; non-negative floats order as their bits)
+__global__ void k_maxabs_f2(const float2* __restrict__ v, int64_t n, unsigned int* __restrict__ out)
+{
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, sqrtf(v[i].x * v[i].x + v[i].y * v[i].y));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// y-pass store into 16-bit pairs, times q
+template <typename T16> struct StoreTo16 {
+    T16* out;
+    int64_t os, s;
+    float q;
+    __device__ __forceinline__ void operator()(float2 v, int64_t o, int64_t i, int j) const
+    {
+        store_cx(out + o * os + i + (int64_t)j * s, make_float2(v.x * q, v.y * q));
+    }
+};
+
+// x-pass epilogue of the 16-bit path: C_alpha(x) = w(x) * value * fac[alpha]
+// * max |G| (undoing the component, image-spectrum and y-pass scales)
+struct SinkNormaliseScaled {
+    float* C;
+    const float* w;
+    const float* fac;
+    const float* gmax;
+    int64_t V;
+    int X;
+    __device__ void operator()(int batch, int64_t row, int x, float v) const
+    {
+        int64_t i = row * X + x;
+        const float g = __ldg(gmax);
+        C[(int64_t)batch * V + i] = __ldg(w + i) * v * (__ldg(fac + batch) * (g > 0.f ? g : 1.f));
+    }
+};
+
+template <typename TS, typename TW>
+void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
+                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st)
+{
+    if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, gmax, oscale, st)) return;
     const int Z = pz.L;
     const int ld = (Z % 2 == 0) ? Z + 1 : Z;
     int W = 16;
     while (W > 2 && (3 * (size_t)W * ld + Z) * sizeof(float2) > 112 * 1024) W /= 2;
     size_t smem = (3 * (size_t)W * ld + Z) * sizeof(float2);
-    set_smem(k_zcorr, smem);
+    set_smem(k_zcorr<TS, TW>, smem);
     int64_t grid = ceil_div(ncols, W);
-    k_zcorr<<<(unsigned)grid, 256, smem, st>>>(G, spec, K, tzn, cz, ncols, out, pz, W, ld);
+    k_zcorr<TS, TW><<<(unsigned)grid, 256, smem, st>>>(G, spec, K, tzn, cz, ncols, out, pz, W, ld, gmax, oscale);
     TTM_LAUNCH_CHECK();
 }
+
+template void launch_zcorr<float2, float2>(const float2*, const float2*, int, int, int, int64_t, float2*,
+                                           const LenPlan&, const float*, float, cudaStream_t);
+template void launch_zcorr<__half2, __half2>(const float2*, const __half2*, int, int, int, int64_t, __half2*,
+                                             const LenPlan&, const float*, float, cudaStream_t);
+template void launch_zcorr<__nv_bfloat162, __nv_bfloat162>(const float2*, const __nv_bfloat162*, int, int, int,
+                                                           int64_t, __nv_bfloat162*, const LenPlan&, const float*,
+                                                           float, cudaStream_t);
 
 void plan_build_spectra(ttm_plan* P, const double* d_field)
 {
@@ -129,18 +206,80 @@ void plan_build_spectra(ttm_plan* P, const double* d_field)
     const int Y = p.Y, X = p.X, Xh = p.Xh, tz = p.tz, ty = p.ty, tx = p.tx;
     const int64_t V = (int64_t)p.Z * Y * X;
     const int64_t ncomp = (int64_t)tz * Y * Xh;
-    P->spec.alloc(P->K * ncomp * sizeof(float2));
+    const bool half = P->prec != TTM_PREC_FP32;
+    P->spec.alloc(P->K * ncomp * (half ? sizeof(__half2) : sizeof(float2)));
     double2* scratch = p.zc.as<double2>();  // tz*Y*Xh <= Z*Y*X
     cudaStream_t st = 0;
+    // 16-bit spectra: the partial spectrum of component alpha is stored
+    // times s_alpha = 1 / max |partial spectrum| (so |stored| <= 1) and the
+    // image spectrum is used divided by max |G|. The z transform of the tz
+    // template rows is then <= tz, so after the inverse z pass |v| <= Z tz
+    // and after the y pass |v| <= Z tz Y (times the z-store factor): the
+    // z- and y-pass stores scale by qz and q to keep these bounds under 2^15.
+    const double bz = (double)p.Z * tz;
+    P->work_qz = half ? (float)std::min(1.0, 32768.0 / bz) : 1.f;
+    P->work_q = half ? (float)std::min(1.0, 32768.0 / (bz * P->work_qz * Y)) : 1.f;
+    std::vector<float> fac(P->K, 1.f);
+    DevBuf part;
+    if (half) part.alloc(256 * sizeof(double));
     for (int a = 0; a < P->K; a++) {
         const double* Ta = d_field + (int64_t)a * tz * ty * tx;
         launch_r2c_any<double>(SrcFieldRows{Ta, Y, X, ty, tx}, (int64_t)tz * Y, scratch, p.px64, st);
         launch_strided_any<double, -1>(scratch, StridedAxis{Xh, tz, (int64_t)Y * Xh, Xh}, p.py64,
                                    ProIdentity<double>(), StoreTo<double>{scratch, (int64_t)Y * Xh, Xh}, st);
-        k_spec_store<<<1024, 256, 0, st>>>(scratch, ncomp, 1.0 / (double)V, P->spec.as<float2>() + a * ncomp);
+        if (!half) {
+            k_spec_store<<<1024, 256, 0, st>>>(scratch, ncomp, 1.0 / (double)V, P->spec.as<float2>() + a * ncomp);
+            TTM_LAUNCH_CHECK();
+            continue;
+        }
+        k_maxabs_d2<<<256, 256, 0, st>>>(scratch, ncomp, part.as<double>());
+        TTM_LAUNCH_CHECK();
+        std::vector<double> hp(256);
+        TTM_CUDA_TRY(cudaMemcpyAsync(hp.data(), part.p, 256 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double v : hp) mx = std::max(mx, v);
+        const double sa = mx > 0.0 ? 1.0 / mx : 1.0;  // on the unnormalised spectrum
+        fac[a] = (float)(1.0 / (V * sa * (double)P->work_qz * (double)P->work_q));
+        if (P->prec == TTM_PREC_FP16_SPECTRA)
+            k_spec_store16<__half2><<<1024, 256, 0, st>>>(scratch, ncomp, sa, P->spec.as<__half2>() + a * ncomp);
+        else
+            k_spec_store16<__nv_bfloat162><<<1024, 256, 0, st>>>(scratch, ncomp, sa,
+                                                                 P->spec.as<__nv_bfloat162>() + a * ncomp);
         TTM_LAUNCH_CHECK();
     }
+    if (half) {
+        P->spec_scale.alloc(P->K * sizeof(float));
+        TTM_CUDA_TRY(cudaMemcpy(P->spec_scale.p, fac.data(), P->K * sizeof(float), cudaMemcpyHostToDevice));
+        P->gmax.alloc(sizeof(float));
+    }
     TTM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// z, y and x passes with 16-bit spectra and work buffer (FP32 arithmetic)
+template <typename T16>
+static void correlate_passes16(ttm_plan* P, float* d_C, cudaStream_t st)
+{
+    Prep& p = P->prep;
+    const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
+    const int64_t ncols = (int64_t)Y * Xh;
+    const int64_t V = (int64_t)Z * Y * X;
+    float* gmax = P->gmax.as<float>();
+    TTM_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(float), st));
+    k_maxabs_f2<<<(unsigned)std::min<int64_t>(ceil_div(Z * ncols, 256), (int64_t)P->ctx->num_sms * 8), 256, 0, st>>>(
+        p.G.as<float2>(), Z * ncols, reinterpret_cast<unsigned int*>(gmax));
+    TTM_LAUNCH_CHECK();
+    T16* work = P->work.as<T16>();
+    launch_zcorr(p.G.as<float2>(), P->spec.as<T16>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32,
+                 (const float*)gmax, P->work_qz, st);
+    stage_end(P, ST_ZCORR, st);
+    launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
+                                  StoreTo16<T16>{work, ncols, Xh, P->work_q}, st);
+    stage_end(P, ST_YPASS, st);
+    launch_c2r_any<float>(work, (int64_t)Z * Y,
+                          SinkNormaliseScaled{d_C, p.w.as<float>(), P->spec_scale.as<float>(), gmax, V, X}, p.px32,
+                          P->K, st);
+    stage_end(P, ST_XPASS, st);
 }
 
 void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st)
@@ -159,8 +298,17 @@ void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st
     stage_end(P, ST_LOCALSUM, st);
     prep_spectrum(p, st);
     stage_end(P, ST_SPECTRUM, st);
+    if (P->prec == TTM_PREC_FP16_SPECTRA) {
+        correlate_passes16<__half2>(P, d_C, st);
+        return;
+    }
+    if (P->prec == TTM_PREC_BF16_SPECTRA) {
+        correlate_passes16<__nv_bfloat162>(P, d_C, st);
+        return;
+    }
     float2* work = P->work.as<float2>();
-    launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32, st);
+    launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32,
+                 (const float*)nullptr, 1.f, st);
     stage_end(P, ST_ZCORR, st);
     launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                               StoreTo<float>{work, ncols, Xh}, st);
@@ -203,7 +351,9 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
         TTM_REQUIRE(out && d_field, E_INVALID_ARG, "null pointer argument");
         TTM_REQUIRE(params_ok(params, why), E_INVALID_ARG, why);
         TTM_REQUIRE(params->dprime == 3, E_UNSUPPORTED, "the GPU path is built for d' = 3");
-        TTM_REQUIRE(precision == TTM_PREC_FP32, E_UNSUPPORTED, "only FP32 spectra are built in this version");
+        TTM_REQUIRE(precision == TTM_PREC_FP32 || precision == TTM_PREC_FP16_SPECTRA ||
+                        precision == TTM_PREC_BF16_SPECTRA,
+                    E_INVALID_ARG, "unknown precision");
         TTM_REQUIRE(tz > 0 && ty > 0 && tx > 0, E_SHAPE, "bad template shape");
         TTM_REQUIRE(mask_fits(tz, params) && mask_fits(ty, params) && mask_fits(tx, params), E_INVALID_ARG,
                     "mask radius (+ soft width) must fit symmetrically inside the template grid");
@@ -217,7 +367,7 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
 
         plan_build_spectra(P, d_field);
         const int64_t Vh = (int64_t)Z * Y * P->prep.Xh;
-        P->work.alloc(P->K * Vh * sizeof(float2));
+        P->work.alloc(P->K * Vh * (precision == TTM_PREC_FP32 ? sizeof(float2) : sizeof(__half2)));
         const int64_t V = (int64_t)Z * Y * X;
         P->cand_cap = V / 8 + 64;  // strict 26-neighbour maxima are >= 2 apart per axis
         P->cand.alloc(P->cand_cap * (sizeof(int64_t) + sizeof(float)));

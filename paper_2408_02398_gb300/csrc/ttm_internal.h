@@ -58,6 +58,12 @@ enum Stage { ST_FILTER = 0, ST_SPECTRUM, ST_LOCALSUM, ST_ZCORR, ST_YPASS, ST_XPA
 void stage_begin(ttm_plan* P, cudaStream_t st);
 void stage_end(ttm_plan* P, int stage, cudaStream_t st);
 
+// fused z pass of the correlation (spectrum / output storage float2, or
+// FP16 / BF16 pairs with the image spectrum scaled by 1 / *gmax)
+template <typename TS, typename TW>
+void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
+                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st);
+
 // host mask on the template grid (Sec. 2 after Eq. 3); returns M
 double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<double>& m);
 
@@ -79,8 +85,11 @@ struct ttm_plan {
     ttm_precision prec = TTM_PREC_FP32;
     ttm::Prep prep;
     ttm::DevBuf spec;        // [K][tz][Y][Xh] partial template spectra (x,y transformed)
-    ttm::DevBuf spec_scale;  // float [K] (reduced-precision spectra)
-    ttm::DevBuf work;        // float2 [K][Z][Y][Xh]
+    ttm::DevBuf spec_scale;  // float [K]: output factor 1 / (s_alpha q) of the 16-bit spectra
+    ttm::DevBuf gmax;        // float [1]: max |G| of the last image spectrum (16-bit spectra)
+    float work_qz = 1.f;     // factor applied at the z-pass store (16-bit spectra)
+    float work_q = 1.f;      // factor applied at the y-pass store (16-bit spectra)
+    ttm::DevBuf work;        // [K][Z][Y][Xh] complex: float2, or FP16 / BF16 pairs
     ttm::DevBuf cand;        // peak candidates
     ttm::DevBuf cand_count;  // unsigned long long [1]
     ttm::DevBuf fb_count;    // unsigned long long [1]: learned-maximiser fallbacks of the last call

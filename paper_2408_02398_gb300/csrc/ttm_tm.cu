@@ -14,8 +14,7 @@
 
 namespace ttm {
 
-void launch_zcorr(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
-                  const LenPlan& pz, cudaStream_t st);
+
 void normalise_template_dev(ttm_ctx* ctx, const float* d_tmpl, int tz, int ty, int tx,
                             const ttm_field_params& fp, DevBuf& tp, cudaStream_t st);
 
@@ -127,7 +126,7 @@ extern "C" ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int
             launch_r2c_any<float>(SrcTemplateRows{rot.as<float>(), Y, X, ty, tx}, (int64_t)tz * Y, pt, p.px32, st);
             launch_strided_any<float, -1>(pt, StridedAxis{Xh, tz, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{pt, ncols, Xh}, st);
-            launch_zcorr(p.G.as<float2>(), pt, 1, tz, tz / 2, ncols, wk, p.pz32, st);
+            launch_zcorr(p.G.as<float2>(), pt, 1, tz, tz / 2, ncols, wk, p.pz32, (const float*)nullptr, 1.f, st);
             launch_strided_any<float, +1>(wk, StridedAxis{Xh, Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{wk, ncols, Xh}, st);
             launch_c2r_any<float>(wk, (int64_t)Z * Y, SinkTMMax{p.w.as<float>(), d_best, d_best_idx, X, (int32_t)j},
