@@ -140,6 +140,19 @@ ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, int tz, int
 ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
                            const ttm_field_params* params, int Z, int Y, int X,
                            ttm_precision precision, ttm_plan** out);
+
+/* As ttm_plan_create, for a Zt x Yt x Xt tomogram correlated on a larger
+ * Z x Y x X working grid (zero padded; each working extent >= the
+ * tomogram's). The FFT lengths are the working extents, so a tomogram of
+ * any size can use lengths with fast transforms (ttm_autotune_shape picks
+ * them). Within the valid box (ttm_plan_valid_box, tomogram coordinates,
+ * which are also working-grid coordinates) the results equal those of an
+ * unpadded plan: no template offset leaves the tomogram there. Every map
+ * (d_C, d_score, ...) is laid out on the working grid; d_tomo passed to
+ * ttm_correlate is the Zt x Yt x Xt tomogram. */
+ttm_status ttm_plan_create_padded(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                                  const ttm_field_params* params, int Zt, int Yt, int Xt, int Z,
+                                  int Y, int X, ttm_precision precision, ttm_plan** out);
 void ttm_plan_destroy(ttm_plan* plan);
 /* Number of components K of the plan. */
 int ttm_plan_components(const ttm_plan* plan);
@@ -295,6 +308,64 @@ ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int Y, int X, 
                         int tz, int ty, int tx, const ttm_field_params* params,
                         const double* h_quats, int64_t n_rot, float* d_best, int32_t* d_best_idx,
                         void* stream);
+
+/* ------------------------------------------ batched TTM and FFT autotuner
+ * (no paper counterpart: an execution scheme for many tomograms) */
+
+/* Autotuner: for each FP32 transform length it times the register kernel
+ * (where one exists) and the shared-memory passes over radix schedules and
+ * tile widths, and keeps the fastest in the context; plans and batches
+ * created afterwards use the tuned schedules. ttm_autotune_shape picks the
+ * working grid (each extent a 7-smooth length in [n, 1.34 n]) of a
+ * Z x Y x X tomogram that minimises the modelled transform time, tuning the
+ * lengths it needs (timed on the device: allocates a scratch buffer and
+ * synchronises). zyx receives 3 ints. */
+ttm_status ttm_autotune_shape(ttm_ctx* ctx, int Z, int Y, int X, int* zyx);
+/* Number of tuned lengths held by the context. */
+int ttm_autotune_entries(const ttm_ctx* ctx);
+/* Tuned records as JSON (one object per line: L, reg, W, rad, us_line);
+ * load replaces records of the same length and rejects malformed files
+ * with TTM_E_INVALID_ARG. */
+ttm_status ttm_autotune_save(const ttm_ctx* ctx, const char* path);
+ttm_status ttm_autotune_load(ttm_ctx* ctx, const char* path);
+
+typedef struct ttm_batch ttm_batch;
+typedef struct {
+    const float* d_tomo; /* float32 [Z][Y][X] (device); read at every ttm_batch_run */
+    int Z, Y, X;
+} ttm_batch_tomo;
+typedef struct {
+    int tomo;        /* index into the tomogram list */
+    int tmpl;        /* index into the field list */
+    float* d_score;  /* float32 [Z][Y][X] of the tomogram (device) */
+    float* d_orient; /* float32 [3][Z][Y][X] */
+    float* d_frob;   /* float32 [Z][Y][X] or NULL */
+} ttm_batch_item;
+enum { TTM_BATCH_AUTOTUNE = 1, TTM_BATCH_LOCALSUM_DF64 = 2 };
+
+/* Batched TTM over (tomogram, template) pairs: all tomograms share
+ * `params` and the template shape tz x ty x tx; d_fields[j] is the
+ * K x tz x ty x tx FP64 field of template j (ttm_build_tensor_field).
+ * Each tomogram is correlated on a zero-padded working grid
+ * (TTM_BATCH_AUTOTUNE: ttm_autotune_shape, else the next 7-smooth extents)
+ * with one preparation shared by its pairs; each pair writes the plain
+ * maximiser's score, orientation (and Frobenius norm) inside its valid box
+ * (tomogram coordinates; other voxels are not written). The pairs run on
+ * n_branches (1..16) concurrent paths, balanced by modelled cost, and the
+ * whole batch is captured once into a CUDA graph. Allocates the
+ * preparations, the spectra of every pair and one work and C buffer per
+ * branch; blocking. TTM_BATCH_LOCALSUM_DF64 selects the double-float local
+ * sums (ttm_plan_set_localsum). */
+ttm_status ttm_batch_create(ttm_ctx* ctx, const ttm_field_params* params, int tz, int ty, int tx,
+                            int n_templates, const double* const* d_fields, int n_tomos,
+                            const ttm_batch_tomo* tomos, int n_items, const ttm_batch_item* items,
+                            int n_branches, int flags, ttm_batch** out);
+/* One launch of the batch's graph on `stream` (asynchronous). Calls on one
+ * batch must not overlap. */
+ttm_status ttm_batch_run(ttm_batch* batch, void* stream);
+/* Working grid chosen for tomogram `tomo` (3 ints). */
+ttm_status ttm_batch_work_shape(const ttm_batch* batch, int tomo, int* zyx);
+void ttm_batch_destroy(ttm_batch* batch);
 
 /* ------------------------------------------------------------ tracing */
 

@@ -42,6 +42,18 @@ TileShape choose_tile(int L, size_t elem_bytes, int min_w, int max_w)
     return t;
 }
 
+TileShape plan_tile(const LenPlan& pl, size_t elem_bytes, int min_w, int max_w)
+{
+    if (pl.tile_w >= min_w && pl.tile_w <= max_w) {
+        TileShape t;
+        t.ld = (pl.L % 2 == 0) ? pl.L + 1 : pl.L;
+        t.W = pl.tile_w;
+        t.smem = (2 * (size_t)t.W * t.ld + pl.L) * elem_bytes;
+        if (t.smem <= 200 * 1024) return t;
+    }
+    return choose_tile(pl.L, elem_bytes, min_w, max_w);
+}
+
 TwiddleCache::~TwiddleCache()
 {
     for (int i = 0; i < n_; i++) cudaFree(entries_[i].ptr);

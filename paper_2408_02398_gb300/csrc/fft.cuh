@@ -42,6 +42,8 @@ struct LenPlan {
     int nst;
     int rad[kMaxStages];
     const void* tw;
+    int tile_w = 0;   // lines per CTA of the shared-memory passes (0: default)
+    int no_reg = 0;   // 1: use the shared-memory passes even where register kernels exist
 };
 
 // sin/cos of 2 pi m / R for the odd radices (mathematical constants)
@@ -391,6 +393,9 @@ struct TileShape {
     size_t smem;
 };
 TileShape choose_tile(int L, size_t elem_bytes, int min_w, int max_w);
+// the plan's tuned tile width if it has one (within the shared-memory
+// budget), else choose_tile
+TileShape plan_tile(const LenPlan& pl, size_t elem_bytes, int min_w, int max_w);
 
 }  // namespace ttm
 
@@ -426,7 +431,7 @@ template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
 inline void launch_strided(const In* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
                            cudaStream_t st)
 {
-    TileShape ts = choose_tile(pl.L, sizeof(cx<R>), 4, 16);
+    TileShape ts = plan_tile(pl, sizeof(cx<R>), 4, 16);
     auto k = k_fft_strided<R, DIR, Pro, Store, In>;
     set_smem(k, ts.smem);
     int64_t grid = ax.outer * ceil_div(ax.inner, ts.W);
@@ -439,7 +444,7 @@ template <typename R, int DIR, class Pro, class Store>
 inline void launch_contig(const cx<R>* in, int64_t nlines, const LenPlan& pl, Pro pro, Store store,
                           cudaStream_t st)
 {
-    TileShape ts = choose_tile(pl.L, sizeof(cx<R>), 1, 8);
+    TileShape ts = plan_tile(pl, sizeof(cx<R>), 1, 8);
     auto k = k_fft_contig<R, DIR, Pro, Store>;
     set_smem(k, ts.smem);
     int64_t grid = ceil_div(nlines, ts.W);
@@ -462,7 +467,7 @@ template <typename R, class Sink, typename In = cx<R>>
 inline void launch_c2r_rows(const In* in, int64_t nrows, Sink sink, const LenPlan& pl, int nbatch,
                             cudaStream_t st)
 {
-    TileShape ts = choose_tile(pl.L, sizeof(cx<R>), 1, 8);
+    TileShape ts = plan_tile(pl, sizeof(cx<R>), 1, 8);
     auto k = k_c2r_rows<R, Sink, In>;
     set_smem(k, ts.smem);
     int64_t grid = ceil_div(nrows, 2 * ts.W) * nbatch;

@@ -402,7 +402,7 @@ inline void launch_strided_any(const In* in, StridedAxis ax, const LenPlan& pl, 
                                cudaStream_t st)
 {
     int E, P;
-    if (!fs_split(pl.L, E, P)) { launch_strided<R, DIR>(in, ax, pl, pro, store, st); return; }
+    if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_strided<R, DIR>(in, ax, pl, pro, store, st); return; }
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \
@@ -422,7 +422,7 @@ inline void launch_contig_any(const cx<R>* in, int64_t nlines, const LenPlan& pl
                               cudaStream_t st)
 {
     int E, P;
-    if (!fs_split(pl.L, E, P)) { launch_contig<R, DIR>(in, nlines, pl, pro, store, st); return; }
+    if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_contig<R, DIR>(in, nlines, pl, pro, store, st); return; }
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \
@@ -439,7 +439,7 @@ template <typename R, class Src>
 inline void launch_r2c_any(Src src, int64_t nrows, cx<R>* out, const LenPlan& pl, cudaStream_t st)
 {
     int E, P;
-    if (!fs_split(pl.L, E, P)) { launch_r2c_rows<R>(src, nrows, out, pl, st); return; }
+    if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_r2c_rows<R>(src, nrows, out, pl, st); return; }
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \
@@ -457,7 +457,7 @@ inline bool launch_zcorr_fs(const float2* G, const TS* spec, int K, int tzn, int
                             const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st)
 {
     int E, P;
-    if (!fs_split(pz.L, E, P)) return false;
+    if (pz.no_reg || !fs_split(pz.L, E, P)) return false;
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<float, E_, P_>;                                                      \
@@ -477,7 +477,7 @@ inline void launch_c2r_any(const In* in, int64_t nrows, Sink sink, const LenPlan
                            cudaStream_t st)
 {
     int E, P;
-    if (!fs_split(pl.L, E, P)) { launch_c2r_rows<R>(in, nrows, sink, pl, nbatch, st); return; }
+    if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_c2r_rows<R>(in, nrows, sink, pl, nbatch, st); return; }
 #define TTM_L(E_, P_)                                                                          \
     {                                                                                          \
         using S = FsShape<R, E_, P_>;                                                          \

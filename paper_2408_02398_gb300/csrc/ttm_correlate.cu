@@ -183,7 +183,7 @@ void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64
     if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, gmax, oscale, st)) return;
     const int Z = pz.L;
     const int ld = (Z % 2 == 0) ? Z + 1 : Z;
-    int W = 16;
+    int W = (pz.tile_w >= 2 && pz.tile_w <= 16) ? pz.tile_w : 16;
     while (W > 2 && (3 * (size_t)W * ld + Z) * sizeof(float2) > 112 * 1024) W /= 2;
     size_t smem = (3 * (size_t)W * ld + Z) * sizeof(float2);
     set_smem(k_zcorr<TS, TW>, smem);
@@ -199,6 +199,37 @@ template void launch_zcorr<__half2, __half2>(const float2*, const __half2*, int,
 template void launch_zcorr<__nv_bfloat162, __nv_bfloat162>(const float2*, const __nv_bfloat162*, int, int, int,
                                                            int64_t, __nv_bfloat162*, const LenPlan&, const float*,
                                                            float, cudaStream_t);
+
+// FP32 partial template spectra of all K components on the grid of p
+// (scaled by 1 / V of the working grid), p.zc as scratch
+void spectra_fp32(Prep& p, int K, const double* d_field, float2* spec, cudaStream_t st)
+{
+    const int Y = p.Y, X = p.X, Xh = p.Xh, tz = p.tz, ty = p.ty, tx = p.tx;
+    const int64_t V = (int64_t)p.Z * Y * X;
+    const int64_t ncomp = (int64_t)tz * Y * Xh;
+    double2* scratch = p.zc.as<double2>();
+    for (int a = 0; a < K; a++) {
+        const double* Ta = d_field + (int64_t)a * tz * ty * tx;
+        launch_r2c_any<double>(SrcFieldRows{Ta, Y, X, ty, tx}, (int64_t)tz * Y, scratch, p.px64, st);
+        launch_strided_any<double, -1>(scratch, StridedAxis{Xh, tz, (int64_t)Y * Xh, Xh}, p.py64,
+                                   ProIdentity<double>(), StoreTo<double>{scratch, (int64_t)Y * Xh, Xh}, st);
+        k_spec_store<<<1024, 256, 0, st>>>(scratch, ncomp, 1.0 / (double)V, spec + a * ncomp);
+        TTM_LAUNCH_CHECK();
+    }
+}
+
+// the three K-component passes of the FP32 correlate (after the per-image
+// preparation of p): fused z pass, y pass, x pass with the w epilogue
+void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st)
+{
+    const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
+    const int64_t ncols = (int64_t)Y * Xh;
+    const int64_t V = (int64_t)Z * Y * X;
+    launch_zcorr(p.G.as<float2>(), spec, K, p.tz, p.tz / 2, ncols, work, p.pz32, (const float*)nullptr, 1.f, st);
+    launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
+                                  StoreTo<float>{work, ncols, Xh}, st);
+    launch_c2r_any<float>(work, (int64_t)Z * Y, SinkNormalise{C, p.w.as<float>(), V, X}, p.px32, K, st);
+}
 
 void plan_build_spectra(ttm_plan* P, const double* d_field)
 {
@@ -344,6 +375,13 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
                                       const ttm_field_params* params, int Z, int Y, int X,
                                       ttm_precision precision, ttm_plan** out)
 {
+    return ttm_plan_create_padded(ctx, d_field, tz, ty, tx, params, Z, Y, X, Z, Y, X, precision, out);
+}
+
+extern "C" ttm_status ttm_plan_create_padded(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                                             const ttm_field_params* params, int Zt, int Yt, int Xt, int Z,
+                                             int Y, int X, ttm_precision precision, ttm_plan** out)
+{
     if (!ctx) return TTM_E_INVALID_ARG;
     ttm_plan* P = nullptr;
     try {
@@ -363,7 +401,7 @@ extern "C" ttm_status ttm_plan_create(ttm_ctx* ctx, const double* d_field, int t
         P->fp = *params;
         P->K = ttm_num_components(params->order_n, params->dprime);
         P->prec = precision;
-        prep_create(ctx, P->prep, Z, Y, X, tz, ty, tx, *params);
+        prep_create(ctx, P->prep, Zt, Yt, Xt, Z, Y, X, tz, ty, tx, *params);
 
         plan_build_spectra(P, d_field);
         const int64_t Vh = (int64_t)Z * Y * P->prep.Xh;
@@ -390,9 +428,9 @@ extern "C" void ttm_plan_valid_box(const ttm_plan* plan, int* b)
 {
     if (!plan || !b) return;
     const Prep& p = plan->prep;
-    b[0] = p.tz / 2; b[1] = p.Z - (p.tz - p.tz / 2) + 1;
-    b[2] = p.ty / 2; b[3] = p.Y - (p.ty - p.ty / 2) + 1;
-    b[4] = p.tx / 2; b[5] = p.X - (p.tx - p.tx / 2) + 1;
+    b[0] = p.tz / 2; b[1] = p.Zt - (p.tz - p.tz / 2) + 1;
+    b[2] = p.ty / 2; b[3] = p.Yt - (p.ty - p.ty / 2) + 1;
+    b[4] = p.tx / 2; b[5] = p.Xt - (p.tx - p.tx / 2) + 1;
 }
 
 extern "C" ttm_status ttm_correlate(ttm_plan* plan, const float* d_tomo, float* d_C, void* stream)

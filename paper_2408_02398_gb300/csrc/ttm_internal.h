@@ -27,7 +27,8 @@ struct DevBuf {
 // Per-tomogram-shape workspace shared by the TTM correlate and the TM
 // baseline: filtered tomogram, its spectrum, FP64 local sums and w.
 struct Prep {
-    int Z = 0, Y = 0, X = 0, Xh = 0;
+    int Zt = 0, Yt = 0, Xt = 0;  // tomogram
+    int Z = 0, Y = 0, X = 0, Xh = 0;  // working grid (>= tomogram; zero padded)
     int tz = 0, ty = 0, tx = 0;
     double M = 0;              // sum of the mask
     double filter_a = 0.2;
@@ -45,7 +46,7 @@ struct Prep {
     LenPlan px32, py32, pz32, px64, py64, pz64, pxd, pyd, pzd;
 };
 
-void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
+void prep_create(ttm_ctx* ctx, Prep& p, int Zt, int Yt, int Xt, int Z, int Y, int X, int tz, int ty, int tx,
                  const ttm_field_params& fp);
 // the three parts of the per-tomogram preparation, in this order:
 // g = h * f (+ variance floor), G = FFT(g), FP64 local sums -> w
@@ -64,13 +65,41 @@ template <typename TS, typename TW>
 void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
                   const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st);
 
+// FP32 partial template spectra (K components) on the grid of p, and the
+// three K-component passes of the FP32 correlate into C [K][Z][Y][X]
+void spectra_fp32(Prep& p, int K, const double* d_field, float2* spec, cudaStream_t st);
+void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st);
+// plain maximiser over box b of C (grid Z x Yin x Xin), maps written on a
+// Zo x Yout x Xout grid at the same coordinates
+void peakmap_box_run(ttm_ctx* ctx, int n, const float* C, int Z, int Yin, int Xin, const int* b, int Zo, int Yout,
+                     int Xout, float* score, float* orient, float* frob, cudaStream_t st);
+void autotune_shape(ttm_ctx* ctx, const int t[3], int out[3]);
+
+// LenPlan of length L and twiddle kind: the autotuned schedule and tile
+// width when the context has one for FP32 L, else the default schedule
+LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind);
+
 // host mask on the template grid (Sec. 2 after Eq. 3); returns M
 double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<double>& m);
 
 }  // namespace ttm
 
+namespace ttm {
+// one autotuned FP32 transform length: the fastest of the register kernel
+// and the shared-memory passes over radix schedules and tile widths
+struct TuneRec {
+    int L = 0;
+    int reg = 0;  // 1: register kernel
+    int W = 0;    // tile width of the shared-memory passes
+    int nst = 0;
+    int rad[kMaxStages] = {};
+    double us_line = 0;  // measured microseconds per line of a strided pass
+};
+}  // namespace ttm
+
 struct ttm_ctx {
     int device = 0;
+    std::vector<ttm::TuneRec> tune;  // autotuner cache
     std::string last_error;
     ttm::TwiddleCache twiddles;
     int num_sms = 0;

@@ -266,20 +266,34 @@ struct ProbeTables {
 };
 
 // which voxels a k_peakmap launch visits
-enum PmMode { PM_ALL = 0, PM_LIST = 1, PM_SWEEP = 2 };
+enum PmMode { PM_ALL = 0, PM_LIST = 1, PM_SWEEP = 2, PM_BOX = 3 };
 
 // PM_ALL: every voxel. PM_LIST: the first min(*list_count, list_cap)
 // entries of list. PM_SWEEP: only if *list_count > list_cap (the list
 // overflowed), every voxel whose score holds the NaN placed there by the
-// learned maximiser.
+// learned maximiser. PM_BOX: the voxels of a box of the C grid (row
+// lengths Yin, Xin), written to a grid with rows Yout, Xout and component
+// stride Vout (the tomogram grid of a zero-padded working grid).
+struct PmGeom {
+    int mode = PM_ALL;
+    const uint32_t* list = nullptr;
+    const unsigned long long* list_count = nullptr;
+    int64_t list_cap = 0;
+    int z0 = 0, y0 = 0, x0 = 0, bz = 0, by = 0, bx = 0;
+    int Yin = 0, Xin = 0, Yout = 0, Xout = 0;
+    int64_t Vout = 0;
+};
+
 template <int N>
 __global__ void __launch_bounds__(kPmThreads)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
-          float* __restrict__ frob, ProbeTables tabs, int mode, const uint32_t* __restrict__ list,
-          const unsigned long long* __restrict__ list_count, int64_t list_cap)
+          float* __restrict__ frob, ProbeTables tabs, PmGeom geo)
 {
-    if (mode == PM_SWEEP && (int64_t)*list_count <= list_cap) return;
-    const int64_t n_items = mode == PM_LIST ? min((int64_t)*list_count, list_cap) : V;
+    const int mode = geo.mode;
+    if (mode == PM_SWEEP && (int64_t)*geo.list_count <= geo.list_cap) return;
+    const int64_t n_items = mode == PM_LIST ? min((int64_t)*geo.list_count, geo.list_cap)
+                          : mode == PM_BOX ? (int64_t)geo.bz * geo.by * geo.bx : V;
+    const int64_t Vo = mode == PM_BOX ? geo.Vout : V;
     constexpr int K = ncomp3(N);
     constexpr int KP = kpad(N);
     constexpr int kStarts = nstarts(N);
@@ -299,9 +313,17 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t - threadIdx.x < n_items;
          t += (int64_t)gridDim.x * blockDim.x) {
         bool ok = t < n_items;
-        int64_t v = t;
-        if (mode == PM_LIST && ok) v = list[t];
+        int64_t v = t, vo = t;
+        if (mode == PM_LIST && ok) vo = v = geo.list[t];
         if (mode == PM_SWEEP && ok) ok = isnan(score[v]);
+        if (mode == PM_BOX && ok) {
+            const int xx = (int)(t % geo.bx);
+            const int64_t r = t / geo.bx;
+            const int yy = (int)(r % geo.by), zz = (int)(r / geo.by);
+            const int z = geo.z0 + zz, y = geo.y0 + yy, x = geo.x0 + xx;
+            v = ((int64_t)z * geo.Yin + y) * geo.Xin + x;
+            vo = ((int64_t)z * geo.Yout + y) * geo.Xout + x;
+        }
         float c[KP];
         float F2 = 0.f;
         {
@@ -396,11 +418,11 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
         // canonical half-sphere: last non-zero of (z, y, x) positive
         if (bz < 0.f || (bz == 0.f && (by < 0.f || (by == 0.f && bx < 0.f)))) { bx = -bx; by = -by; bz = -bz; }
         if (ok) {
-            score[v] = best;
-            orient[v] = bx;
-            orient[V + v] = by;
-            orient[2 * V + v] = bz;
-            if (frob) frob[v] = F;
+            score[vo] = best;
+            orient[vo] = bx;
+            orient[Vo + vo] = by;
+            orient[2 * Vo + vo] = bz;
+            if (frob) frob[vo] = F;
         }
     }
 }
@@ -624,10 +646,11 @@ static ProbeTables probe_tables(ttm_ctx* ctx)
 
 // plain maximiser over all voxels (PM_ALL) or the learned path's fallbacks
 static void plain_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
-                      int mode, const uint32_t* list, const unsigned long long* count, int64_t cap, cudaStream_t st)
+                      const PmGeom& geo, cudaStream_t st)
 {
     const ProbeTables t = probe_tables(ctx);
-    const int64_t blocks = ceil_div(V, kPmThreads);
+    const int64_t items = geo.mode == PM_BOX ? (int64_t)geo.bz * geo.by * geo.bx : V;
+    const int64_t blocks = std::max<int64_t>(1, ceil_div(items, kPmThreads));
     const size_t smem = (size_t)kProbes * kPmThreads * sizeof(__half);
     // enough CTAs to fill every SM several times, then a grid stride
     const int64_t grid = std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 32);
@@ -635,7 +658,7 @@ static void plain_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* sco
     // total, so the dynamic size is always declared
 #define TTM_PM_LAUNCH(N_)                                                                          \
     TTM_CUDA_TRY(cudaFuncSetAttribute(k_peakmap<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k_peakmap<N_><<<(unsigned)grid, kPmThreads, smem, st>>>(C, V, score, orient, frob, t, mode, list, count, cap);
+    k_peakmap<N_><<<(unsigned)grid, kPmThreads, smem, st>>>(C, V, score, orient, frob, t, geo);
     switch (n) {
         case 2: TTM_PM_LAUNCH(2); break;
         case 4: TTM_PM_LAUNCH(4); break;
@@ -649,7 +672,22 @@ static void plain_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* sco
 void peakmap_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
                  cudaStream_t st)
 {
-    plain_run(ctx, n, C, V, score, orient, frob, PM_ALL, nullptr, nullptr, 0, st);
+    plain_run(ctx, n, C, V, score, orient, frob, PmGeom(), st);
+}
+
+// plain maximiser over box b (z0, z1, y0, y1, x0, x1) of C on a Z x Yin x
+// Xin grid, maps written on a Zo x Yout x Xout grid at the same coordinates
+void peakmap_box_run(ttm_ctx* ctx, int n, const float* C, int Z, int Yin, int Xin, const int* b, int Zo, int Yout,
+                     int Xout, float* score, float* orient, float* frob, cudaStream_t st)
+{
+    PmGeom g;
+    g.mode = PM_BOX;
+    g.z0 = b[0]; g.y0 = b[2]; g.x0 = b[4];
+    g.bz = b[1] - b[0]; g.by = b[3] - b[2]; g.bx = b[5] - b[4];
+    g.Yin = Yin; g.Xin = Xin; g.Yout = Yout; g.Xout = Xout;
+    g.Vout = (int64_t)Zo * Yout * Xout;
+    if (g.bz <= 0 || g.by <= 0 || g.bx <= 0) return;
+    plain_run(ctx, n, C, (int64_t)Z * Yin * Xin, score, orient, frob, g, st);
 }
 
 // learned maximiser, then the plain one on its rejected voxels
@@ -681,8 +719,14 @@ static void peakmap_learned_run(ttm_plan* P, ttm_mlp* M, const float* C, int64_t
     }
 #undef TTM_ML_LAUNCH
     TTM_LAUNCH_CHECK();
-    plain_run(ctx, n, C, V, score, orient, frob, PM_LIST, list, count, cap, st);
-    plain_run(ctx, n, C, V, score, orient, frob, PM_SWEEP, list, count, cap, st);
+    PmGeom g;
+    g.list = list;
+    g.list_count = count;
+    g.list_cap = cap;
+    g.mode = PM_LIST;
+    plain_run(ctx, n, C, V, score, orient, frob, g, st);
+    g.mode = PM_SWEEP;
+    plain_run(ctx, n, C, V, score, orient, frob, g, st);
 }
 
 }  // namespace ttm

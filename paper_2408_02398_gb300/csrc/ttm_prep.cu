@@ -60,33 +60,38 @@ constexpr int kPreThreads = 256;
 // (the input is FP32), written as g (f32) and as (g, g^2) in FP64 or as
 // double-float pairs for the local sums; per-block partial sums of g^2 for
 // the variance floor.
+// The tomogram f is Zt x Yt x Xt; g lives on the working grid Z x Y x X
+// (>= the tomogram on every axis, zero beyond it apart from the filter's
+// one-voxel spill). Only tomogram voxels enter the g^2 partial sums.
 template <bool DF>
 __global__ void __launch_bounds__(kPreThreads)
-k_prefilter(const float* __restrict__ f, int Z, int Y, int X, float a, float* __restrict__ g32,
-            double2* __restrict__ zc, double* __restrict__ partials)
+k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, int X, float a,
+            float* __restrict__ g32, double2* __restrict__ zc, double* __restrict__ partials)
 {
     __shared__ float warp_sums[kPreThreads / 32];
     const int64_t V = (int64_t)Z * Y * X;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float g = 0.f;
+    bool in_tomo = false;
     if (v < V) {
         const int x = (int)(v % X);
         const int64_t t = v / X;
         const int y = (int)(t % Y);
         const int z = (int)(t / Y);
+        in_tomo = z < Zt && y < Yt && x < Xt;
         const float tap[3] = {a, 1.f - 2.f * a, a};
 #pragma unroll
         for (int dz = -1; dz <= 1; dz++) {
             const int zz = z + dz;
-            if (zz < 0 || zz >= Z) continue;
+            if (zz < 0 || zz >= Zt) continue;
 #pragma unroll
             for (int dy = -1; dy <= 1; dy++) {
                 const int yy = y + dy;
-                if (yy < 0 || yy >= Y) continue;
-                const float* row = f + ((int64_t)zz * Y + yy) * X;
-                float r = tap[1] * __ldg(row + x);
-                if (x > 0) r += tap[0] * __ldg(row + x - 1);
-                if (x + 1 < X) r += tap[2] * __ldg(row + x + 1);
+                if (yy < 0 || yy >= Yt) continue;
+                const float* row = f + ((int64_t)zz * Yt + yy) * Xt;
+                float r = x < Xt ? tap[1] * __ldg(row + x) : 0.f;
+                if (x > 0 && x - 1 < Xt) r += tap[0] * __ldg(row + x - 1);
+                if (x + 1 < Xt) r += tap[2] * __ldg(row + x + 1);
                 g += tap[dz + 1] * tap[dy + 1] * r;
             }
         }
@@ -100,7 +105,7 @@ k_prefilter(const float* __restrict__ f, int Z, int Y, int X, float a, float* __
             zc[v] = make_double2(gd, gd * gd);
         }
     }
-    float sq = g * g;
+    float sq = in_tomo ? g * g : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = sq;
@@ -239,17 +244,19 @@ __global__ void k_octant_to_df(const double* __restrict__ in, int64_t n, float2*
 
 // ---------------------------------------------------------------- host --
 
-void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int tx,
+void prep_create(ttm_ctx* ctx, Prep& p, int Zt, int Yt, int Xt, int Z, int Y, int X, int tz, int ty, int tx,
                  const ttm_field_params& fp)
 {
-    TTM_REQUIRE(Z >= tz && Y >= ty && X >= tx, E_SHAPE, "tomogram smaller than the template");
-    TTM_REQUIRE(Z >= 2 && Y >= 2 && X >= 2, E_SHAPE, "each tomogram axis needs at least 2 voxels");
+    TTM_REQUIRE(Zt >= tz && Yt >= ty && Xt >= tx, E_SHAPE, "tomogram smaller than the template");
+    TTM_REQUIRE(Zt >= 2 && Yt >= 2 && Xt >= 2, E_SHAPE, "each tomogram axis needs at least 2 voxels");
+    TTM_REQUIRE(Z >= Zt && Y >= Yt && X >= Xt, E_SHAPE, "working grid smaller than the tomogram");
+    p.Zt = Zt; p.Yt = Yt; p.Xt = Xt;
     p.Z = Z; p.Y = Y; p.X = X; p.Xh = X / 2 + 1;
     p.tz = tz; p.ty = ty; p.tx = tx;
     p.filter_a = fp.filter_a;
-    p.px32 = make_len_plan(ctx->twiddles, X, TW_F32);
-    p.py32 = make_len_plan(ctx->twiddles, Y, TW_F32);
-    p.pz32 = make_len_plan(ctx->twiddles, Z, TW_F32);
+    p.px32 = ctx_len_plan(ctx, X, TW_F32);
+    p.py32 = ctx_len_plan(ctx, Y, TW_F32);
+    p.pz32 = ctx_len_plan(ctx, Z, TW_F32);
     p.px64 = make_len_plan(ctx->twiddles, X, TW_F64);
     p.py64 = make_len_plan(ctx->twiddles, Y, TW_F64);
     p.pz64 = make_len_plan(ctx->twiddles, Z, TW_F64);
@@ -293,17 +300,17 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Z, int Y, int X, int tz, int ty, int
 
 void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st)
 {
-    const int64_t V = (int64_t)p.Z * p.Y * p.X;
+    const int64_t Vt = (int64_t)p.Zt * p.Yt * p.Xt;
     if (p.localsum_mode == 1)
-        k_prefilter<true><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
-                                                                     p.g32.as<float>(), p.zc.as<double2>(),
-                                                                     p.partials.as<double>());
+        k_prefilter<true><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Zt, p.Yt, p.Xt, p.Z, p.Y, p.X,
+                                                                     (float)p.filter_a, p.g32.as<float>(),
+                                                                     p.zc.as<double2>(), p.partials.as<double>());
     else
-        k_prefilter<false><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Z, p.Y, p.X, (float)p.filter_a,
-                                                                      p.g32.as<float>(), p.zc.as<double2>(),
-                                                                      p.partials.as<double>());
+        k_prefilter<false><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Zt, p.Yt, p.Xt, p.Z, p.Y, p.X,
+                                                                      (float)p.filter_a, p.g32.as<float>(),
+                                                                      p.zc.as<double2>(), p.partials.as<double>());
     TTM_LAUNCH_CHECK();
-    k_var_floor<<<1, 1024, 0, st>>>(p.partials.as<double>(), p.nblk_pre, V, p.M, p.floor.as<double>());
+    k_var_floor<<<1, 1024, 0, st>>>(p.partials.as<double>(), p.nblk_pre, Vt, p.M, p.floor.as<double>());
     TTM_LAUNCH_CHECK();
 }
 

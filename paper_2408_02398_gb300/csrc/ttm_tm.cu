@@ -97,7 +97,7 @@ extern "C" ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int
         TTM_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = (cudaStream_t)stream;
         Prep p;
-        prep_create(ctx, p, Z, Y, X, tz, ty, tx, *params);
+        prep_create(ctx, p, Z, Y, X, Z, Y, X, tz, ty, tx, *params);
         DevBuf tp;
         normalise_template_dev(ctx, d_tmpl, tz, ty, tx, *params, tp, st);
         const int Xh = p.Xh;

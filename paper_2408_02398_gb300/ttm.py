@@ -22,6 +22,7 @@ STATUS = {0: "TTM_OK", 1: "TTM_E_INVALID_ARG", 2: "TTM_E_SHAPE", 3: "TTM_E_UNSUP
 TTM_PREC_FP32, TTM_PREC_FP16_SPECTRA, TTM_PREC_BF16_SPECTRA = 0, 1, 2
 TTM_MAX_PLAIN, TTM_MAX_MLP_WARM = 0, 1
 TTM_LOCALSUM_FP64, TTM_LOCALSUM_DF64 = 0, 1
+TTM_BATCH_AUTOTUNE, TTM_BATCH_LOCALSUM_DF64 = 1, 2
 
 # every symbol include/ttm.h declares
 EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_error", "ttm_num_components",
@@ -32,7 +33,9 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_
            "ttm_find_peaks_noalloc", "ttm_plan_fallback_count", "ttm_mlp_num_params", "ttm_mlp_create",
            "ttm_mlp_destroy", "ttm_mlp_inputs", "ttm_mlp_get_params", "ttm_mlp_set_params", "ttm_mlp_forward",
            "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
-           "ttm_mlp_load"]
+           "ttm_mlp_load", "ttm_plan_create_padded", "ttm_autotune_shape", "ttm_autotune_entries",
+           "ttm_autotune_save", "ttm_autotune_load", "ttm_batch_create", "ttm_batch_run", "ttm_batch_work_shape",
+           "ttm_batch_destroy"]
 
 
 class TTMError(RuntimeError):
@@ -101,6 +104,17 @@ def lib():
             "ttm_mlp_make_pairs": (_i, [_vp, _vp, _i, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
             "ttm_mlp_save": (_i, [_vp, C.c_char_p]),
             "ttm_mlp_load": (_i, [_vp, C.c_char_p, C.POINTER(_vp)]),
+            "ttm_plan_create_padded": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(ttm_field_params), _i, _i, _i, _i, _i,
+                                            _i, _i, C.POINTER(_vp)]),
+            "ttm_autotune_shape": (_i, [_vp, _i, _i, _i, _vp]),
+            "ttm_autotune_entries": (_i, [_vp]),
+            "ttm_autotune_save": (_i, [_vp, C.c_char_p]),
+            "ttm_autotune_load": (_i, [_vp, C.c_char_p]),
+            "ttm_batch_create": (_i, [_vp, C.POINTER(ttm_field_params), _i, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i,
+                                      _i, C.POINTER(_vp)]),
+            "ttm_batch_run": (_i, [_vp, _vp]),
+            "ttm_batch_work_shape": (_i, [_vp, _i, _vp]),
+            "ttm_batch_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -202,14 +216,18 @@ def ttm_build_tensor_field(ctx: Context, d_tmpl, p: ttm_field_params, d_field, s
 class Plan:
     """ttm_plan: a tensor field bound to one tomogram shape."""
 
-    def __init__(self, ctx: Context, d_field, p: ttm_field_params, shape, precision=TTM_PREC_FP32):
+    def __init__(self, ctx: Context, d_field, p: ttm_field_params, shape, precision=TTM_PREC_FP32,
+                 work_shape=None):
         import torch
         K, tz, ty, tx = d_field.shape
         Z, Y, X = shape
+        Zw, Yw, Xw = shape if work_shape is None else work_shape
         h = _vp()
-        ctx.check(lib().ttm_plan_create(ctx.h, _dev(d_field, torch.float64, "d_field"), tz, ty, tx, C.byref(p),
-                                        Z, Y, X, precision, C.byref(h)))
-        self.h, self.ctx, self.shape, self.K = h, ctx, (Z, Y, X), lib().ttm_plan_components(h)
+        ctx.check(lib().ttm_plan_create_padded(ctx.h, _dev(d_field, torch.float64, "d_field"), tz, ty, tx,
+                                               C.byref(p), Z, Y, X, Zw, Yw, Xw, precision, C.byref(h)))
+        self.h, self.ctx, self.K = h, ctx, lib().ttm_plan_components(h)
+        self.tomo_shape = (Z, Y, X)
+        self.shape = (Zw, Yw, Xw)   # working grid: the layout of every map
         self.tshape = (tz, ty, tx)
         self.params = p
 
@@ -342,6 +360,73 @@ def ttm_mlp_make_pairs(ctx: Context, d_C, order_n: int, d_orient, d_idx, d_X, d_
                                        _dev(d_orient, torch.float32, "d_orient"), _dev(d_idx, torch.int64, "d_idx"),
                                        d_idx.shape[0], _dev(d_X, torch.float32, "d_X"),
                                        _dev(d_U, torch.float32, "d_U"), _stream(stream)))
+
+
+# -------------------------------------------------- autotuner and batches --
+
+def ttm_autotune_shape(ctx: Context, shape) -> tuple:
+    out = (C.c_int * 3)()
+    ctx.check(lib().ttm_autotune_shape(ctx.h, int(shape[0]), int(shape[1]), int(shape[2]), out))
+    return tuple(out)
+
+
+def ttm_autotune_entries(ctx: Context) -> int:
+    return lib().ttm_autotune_entries(ctx.h)
+
+
+def ttm_autotune_save(ctx: Context, path: str):
+    ctx.check(lib().ttm_autotune_save(ctx.h, path.encode()))
+
+
+def ttm_autotune_load(ctx: Context, path: str):
+    ctx.check(lib().ttm_autotune_load(ctx.h, path.encode()))
+
+
+class ttm_batch_tomo(C.Structure):
+    _fields_ = [("d_tomo", _vp), ("Z", _i), ("Y", _i), ("X", _i)]
+
+
+class ttm_batch_item(C.Structure):
+    _fields_ = [("tomo", _i), ("tmpl", _i), ("d_score", _vp), ("d_orient", _vp), ("d_frob", _vp)]
+
+
+class Batch:
+    """ttm_batch: (tomogram, template) pairs in one captured CUDA graph.
+    tomos: CUDA float32 [Z][Y][X] tensors; fields: CUDA float64 [K][t][t][t]
+    tensors; items: (tomo, tmpl, d_score, d_orient, d_frob or None) with
+    maps on the tomogram grid (only the valid box is written)."""
+
+    def __init__(self, ctx: Context, p: ttm_field_params, fields, tomos, items, n_branches=4,
+                 flags=TTM_BATCH_AUTOTUNE):
+        import torch
+        self.ctx = ctx
+        self._keep = (list(fields), list(tomos), list(items))
+        tz, ty, tx = fields[0].shape[1:]
+        fptr = (C.c_void_p * len(fields))(*[_dev(f, torch.float64, "field") for f in fields])
+        tarr = (ttm_batch_tomo * len(tomos))(*[ttm_batch_tomo(_dev(t, torch.float32, "tomo"), *t.shape)
+                                              for t in tomos])
+        iarr = (ttm_batch_item * len(items))(*[
+            ttm_batch_item(a, b, _dev(s, torch.float32, "d_score"), _dev(o, torch.float32, "d_orient"),
+                           None if f is None else _dev(f, torch.float32, "d_frob")) for a, b, s, o, f in items])
+        h = _vp()
+        ctx.check(lib().ttm_batch_create(ctx.h, C.byref(p), tz, ty, tx, len(fields), fptr, len(tomos), tarr,
+                                         len(items), iarr, n_branches, flags, C.byref(h)))
+        self.h = h
+
+    def run(self, stream=None):
+        self.ctx.check(lib().ttm_batch_run(self.h, _stream(stream)))
+
+    def work_shape(self, i: int) -> tuple:
+        out = (C.c_int * 3)()
+        self.ctx.check(lib().ttm_batch_work_shape(self.h, i, out))
+        return tuple(out)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ttm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
 
 
 def ttm_find_peaks(plan: Plan, d_map, P: int, min_dist: float, stream=None):
