@@ -304,6 +304,302 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- the three other forms --
+#
+# Each prints one JSON line with the form's throughput as `value` and the
+# plain FP32 form measured in the same run beside it (`plain`), plus the
+# stated error. They are not the default workload.
+
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _crop_voxels(shape, tshape, edge, count, seed):
+    """Random valid-interior voxels of the centred edge^3 crop."""
+    import oracle as O
+    vox = O.valid_voxels(shape, tshape)
+    z, y, x = np.unravel_index(vox, shape)
+    c = [d // 2 for d in shape]
+    sel = (np.abs(z - c[0]) < edge // 2) & (np.abs(y - c[1]) < edge // 2) & (np.abs(x - c[2]) < edge // 2)
+    v = vox[sel]
+    return np.sort(np.random.default_rng(seed).choice(v, min(count, v.size), replace=False))
+
+
+def run_mixed(args):
+    """Order 6 on 1024 x 1024 x 256 (48^3 template, r = 19, 2000 copies at
+    SNR 0.05): FP32, FP16 and BF16 spectra; error against the FP64 oracle at
+    sampled valid voxels of the centred 128^3 crop (the oracle uses its own
+    field; both sides use 24 x 64 rotations, which the per-tomogram kernels
+    do not depend on)."""
+    import torch
+    from paper_2408_02398_gb300 import build, synth
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    import oracle as O
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    wl = synth.workload_order6()
+    gen_s = time.perf_counter() - t0
+    Z, Y, X = wl.tomo.shape
+    V = Z * Y * X
+    n, r = wl.order_n, wl.mask_radius
+    K = ttm.ttm_num_components(n)
+    ctx = ttm.Context(0)
+    p = ttm.params(order_n=n, mask_radius=r, n_rot_base=64)
+    t = torch.as_tensor(wl.template, device=dev)
+    field = torch.empty((K,) + wl.template.shape, dtype=torch.float64, device=dev)
+    ttm.ttm_build_tensor_field(ctx, t, p, field)
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    C = torch.empty((K, Z, Y, X), device=dev)
+    score = torch.empty((Z, Y, X), device=dev)
+    orient = torch.empty((3, Z, Y, X), device=dev)
+    vox = _crop_voxels((Z, Y, X), wl.template.shape, 128, args.crop_voxels, 7)
+    tv = torch.as_tensor(vox, device=dev)
+    pr = O.Prepared(wl.tomo, wl.template, r)
+    ofield = O.tensor_field(pr.tp, O.rotation_set(64), n, 3)
+    w, _, _ = O.local_w(pr.g, pr.m, vox, False, pr.floor)
+    Cref = O.correlate(pr.g, ofield, vox, False, w)
+    sref, _, _ = O.maximise(Cref, n, 3, 20000)
+    stream = torch.cuda.current_stream()
+    forms = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, prec in (("fp32", ttm.TTM_PREC_FP32), ("fp16", ttm.TTM_PREC_FP16_SPECTRA),
+                       ("bf16", ttm.TTM_PREC_BF16_SPECTRA)):
+        plan = ttm.Plan(ctx, field, p, (Z, Y, X), precision=prec)
+        ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
+        ms_corr = _timed(lambda: ttm.ttm_correlate(plan, d_tomo, C), args.steps, args.warmup, stream)
+        ms_pm = _timed(lambda: ttm.ttm_peak_map(plan, C, score, orient), args.steps, args.warmup, stream)
+        got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
+        sg = score.flatten()[tv].cpu().numpy()
+        forms[name] = {"correlate_ms": ms_corr, "peak_map_ms": ms_pm, "voxels_per_s": V / ((ms_corr + ms_pm) / 1e3),
+                       "correlate_voxels_per_s": V / (ms_corr / 1e3),
+                       "C_max_abs_err": float(np.abs(got - Cref).max()),
+                       "C_rel_l2_err": float(np.linalg.norm(got - Cref) / np.linalg.norm(Cref)),
+                       "C_max_abs": float(np.abs(Cref).max()),
+                       "score_max_abs_err": float(np.abs(sg - sref).max())}
+        del plan
+    ck = clocks.stop()
+    pk, how = peaks_file()
+    f16 = forms["fp16"]
+    alg = (4 + 4 * K) * V
+    line = {"metric": METRIC + ", FP16 spectra form", "value": f16["voxels_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f16["correlate_ms"] + f16["peak_map_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage / f32 math",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "shape_zyx": [Z, Y, X], "template": 48, "order_n": n, "components": K,
+                       "mask_radius": r, "copies_planted": int(len(wl.planted.centres)), "snr": 0.05,
+                       "rotations_field": 24 * 64, "local_sums": "double-float",
+                       "error_sample": "%d valid voxels of the centred 128^3 crop" % vox.size,
+                       "generation_s": gen_s},
+            "forms": forms,
+            "vs_plain_fp32": {"whole_step": f16["voxels_per_s"] / forms["fp32"]["voxels_per_s"],
+                              "correlate": forms["fp32"]["correlate_ms"] / f16["correlate_ms"],
+                              "bf16_correlate": forms["fp32"]["correlate_ms"] / forms["bf16"]["correlate_ms"]},
+            "roofline_correlate": {"bound": "hbm", "achieved": alg / (f16["correlate_ms"] / 1e3) / 1e9,
+                                   "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s", "peak_source": how,
+                                   "traffic": None, "bytes_per_voxel": 4 + 4 * K},
+            "clocks": ck}
+    line["roofline_correlate"]["frac"] = line["roofline_correlate"]["achieved"] / line["roofline_correlate"]["peak"]
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Order 6 on the same 1024 x 1024 x 256 volume: the network is trained
+    on 10^6 (C / ||C||_F, plain maximiser direction) pairs from a separate
+    seeded 160^3 tomogram with the same template, then the learned
+    maximiser is timed against the plain one on the big volume and judged
+    by it over every valid voxel."""
+    import torch
+    from paper_2408_02398_gb300 import build, synth
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    wl = synth.workload_order6()
+    gen_s = time.perf_counter() - t0
+    Z, Y, X = wl.tomo.shape
+    V = Z * Y * X
+    n, r = wl.order_n, wl.mask_radius
+    K = ttm.ttm_num_components(n)
+    ctx = ttm.Context(0)
+    p = ttm.params(order_n=n, mask_radius=r, n_rot_base=2048)
+    stream = torch.cuda.current_stream()
+    # training pairs
+    tshape = (160, 160, 160)
+    tvol, _ = synth.make_tomogram(tshape, wl.template, r, 60, 20240905, snr=0.05)
+    Mt = ttm.Matcher(ctx, wl.template, p, tshape, device=dev)
+    Mt.run(torch.as_tensor(tvol, device=dev))
+    b = Mt.plan.valid_box()
+    zz, yy, xx = np.meshgrid(np.arange(b[0], b[1]), np.arange(b[2], b[3]), np.arange(b[4], b[5]), indexing="ij")
+    idx = ((zz * tshape[1] + yy) * tshape[2] + xx).ravel()
+    idx = np.random.default_rng(1).choice(idx, min(10 ** 6, idx.size), replace=False)
+    dX = torch.empty((idx.size, K), device=dev)
+    dU = torch.empty((idx.size, 3), device=dev)
+    ttm.ttm_mlp_make_pairs(ctx, Mt.C, n, Mt.orient, torch.as_tensor(idx, device=dev), dX, dU)
+    net = ttm.Mlp(ctx, K, seed=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ep in range(20):
+        loss = net.train(dX, dU, epochs=1, batch=4096, lr=1e-3, seed=100 + ep)
+    for ep in range(10):
+        loss = net.train(dX, dU, epochs=1, batch=4096, lr=3e-4, seed=200 + ep)
+    train_s = time.perf_counter() - t0
+    field = Mt.field
+    del Mt, dX, dU
+    torch.cuda.empty_cache()
+    # the big volume
+    plan = ttm.Plan(ctx, field, p, (Z, Y, X))
+    ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    C = torch.empty((K, Z, Y, X), device=dev)
+    sp = torch.empty((Z, Y, X), device=dev)
+    op = torch.empty((3, Z, Y, X), device=dev)
+    sl = torch.empty((Z, Y, X), device=dev)
+    ol = torch.empty((3, Z, Y, X), device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_corr = _timed(lambda: ttm.ttm_correlate(plan, d_tomo, C), args.steps, args.warmup, stream)
+    ms_plain = _timed(lambda: ttm.ttm_peak_map(plan, C, sp, op), args.steps, args.warmup, stream)
+    launches0 = ttm.ttm_kernel_launches()
+    ms_learn = _timed(lambda: ttm.ttm_peak_map(plan, C, sl, ol, mlp=net), args.steps, args.warmup, stream)
+    launches = (ttm.ttm_kernel_launches() - launches0) / (args.steps + args.warmup)
+    ck = clocks.stop()
+    fb = ttm.ttm_plan_fallback_count(plan)
+    bb = plan.valid_box()
+    d = (sl - sp)[bb[0]:bb[1], bb[2]:bb[3], bb[4]:bb[5]]
+    viol = int((d < -1e-4).sum())
+    nvalid = d.numel()
+    # orientation agreement where the scores agree
+    ang = torch.rad2deg(torch.acos(torch.clamp((ol * op).sum(0).abs(), 0, 1)))[bb[0]:bb[1], bb[2]:bb[3], bb[4]:bb[5]]
+    vl = V / ((ms_corr + ms_learn) / 1e3)
+    vp = V / ((ms_corr + ms_plain) / 1e3)
+    mlp_flops = 2.0 * (K * 128 + 128 * 128 + 128 * 3) * V
+    line = {"metric": METRIC + ", learned warm-start form", "value": vl, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_corr + ms_learn,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (MLP bf16)",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "shape_zyx": [Z, Y, X], "order_n": n, "components": K,
+                       "mlp": "%d-128-128-3 GELU(tanh), unit output" % K, "train_pairs": int(idx.size),
+                       "train_volume": "160^3, same template, seed 20240905", "epochs": 30,
+                       "generation_s": gen_s},
+            "plain": {"value": vp, "peak_map_ms": ms_plain},
+            "learned": {"peak_map_ms": ms_learn, "correlate_ms": ms_corr, "train_s": train_s,
+                        "final_batch_loss": loss, "fallback_voxels": fb, "fallback_frac": fb / V,
+                        "kernel_launches_per_call": launches},
+            "judge": {"valid_voxels": nvalid, "violations_below_plain_1e-4": viol,
+                      "min_score_diff": float(d.min().item()), "max_score_diff": float(d.max().item()),
+                      "orientation_deg_p99": float(torch.quantile(ang.flatten()[::97].float(), 0.99).item())},
+            "vs_plain": {"whole_step": vl / vp, "peak_map": ms_plain / ms_learn},
+            "roofline_mlp": {"bound": "tensor", "achieved": mlp_flops / (ms_learn / 1e3) / 1e12,
+                             "peak": float(peaks_file()[0].get("bf16_tflops", 1900.0)), "unit": "TFLOP/s",
+                             "note": "network flops only over the whole learned maximiser time (mma.sync BF16)"},
+            "clocks": ck}
+    line["roofline_mlp"]["frac"] = line["roofline_mlp"]["achieved"] / line["roofline_mlp"]["peak"]
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """64 sub-tomograms of uneven sizes (each axis uniform in 96..256) x 8
+    templates (32^3, r = 12, order 4): the batched form (autotuned working
+    grids, one preparation per sub-tomogram, valid-box maximiser, concurrent
+    branches, one graph launch) against the plain form (one padded plan per
+    pair, correlate + whole-grid maximiser in sequence) on the first
+    `--plain-tomos` sub-tomograms."""
+    import torch
+    from paper_2408_02398_gb300 import build, synth
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    wl = synth.workload_batched()
+    gen_s = time.perf_counter() - t0
+    n, r = wl.order_n, wl.mask_radius
+    K = ttm.ttm_num_components(n)
+    ctx = ttm.Context(0)
+    p = ttm.params(order_n=n, mask_radius=r, n_rot_base=2048)
+    fields = []
+    for tm in wl.templates:
+        f = torch.empty((K,) + tm.shape, dtype=torch.float64, device=dev)
+        ttm.ttm_build_tensor_field(ctx, torch.as_tensor(tm, device=dev), p, f)
+        fields.append(f)
+    tomos = [torch.as_tensor(t, device=dev) for t in wl.tomos]
+    items = []
+    for i, t in enumerate(wl.tomos):
+        for j in range(len(fields)):
+            items.append((i, j, torch.empty(t.shape, device=dev), torch.empty((3,) + t.shape, device=dev), None))
+    vox_total = sum(int(np.prod(t.shape)) for t in wl.tomos) * len(fields)
+    t0 = time.perf_counter()
+    B = ttm.Batch(ctx, p, fields, tomos, items, n_branches=args.branches,
+                  flags=ttm.TTM_BATCH_AUTOTUNE | ttm.TTM_BATCH_LOCALSUM_DF64)
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = ttm.ttm_kernel_launches()
+    ms_b = _timed(lambda: B.run(), args.steps, args.warmup, stream)
+    ck = clocks.stop()
+    vb = vox_total / (ms_b / 1e3)
+    # plain form on a subset
+    sub = list(range(min(args.plain_tomos, len(wl.tomos))))
+    ms_p = 0.0
+    vox_p = 0
+    for i in sub:
+        shape = wl.tomos[i].shape
+        work = tuple(next_smooth7(d) for d in shape)
+        for j in range(len(fields)):
+            plan = ttm.Plan(ctx, fields[j], p, shape, work_shape=work)
+            ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
+            Cw = torch.empty((K,) + work, device=dev)
+            sw = torch.empty(work, device=dev)
+            ow = torch.empty((3,) + work, device=dev)
+
+            def step():
+                ttm.ttm_correlate(plan, tomos[i], Cw)
+                ttm.ttm_peak_map(plan, Cw, sw, ow)
+            ms_p += _timed(step, max(1, args.steps // 2), 1, stream)
+            vox_p += int(np.prod(shape))
+            del plan, Cw, sw, ow
+    vp = vox_p / (ms_p / 1e3)
+    sizes = [t.shape for t in wl.tomos]
+    works = [B.work_shape(i) for i in range(len(wl.tomos))]
+    line = {"metric": METRIC + ", batched form", "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "pairs": len(items), "voxels_per_step": vox_total,
+                       "order_n": n, "components": K, "template": 32, "mask_radius": r,
+                       "branches": args.branches, "copies_planted": int(sum(wl.copies)),
+                       "mean_padding": float(np.mean([np.prod(w) / np.prod(s) for w, s in zip(works, sizes)])),
+                       "create_s": create_s, "generation_s": gen_s, "autotuned_lengths": ttm.ttm_autotune_entries(ctx)},
+            "plain": {"value": vp, "pairs": len(sub) * len(fields),
+                      "note": "one plan per pair on the next 7-smooth grid, correlate + whole-grid maximiser"},
+            "vs_plain": vb / vp, "graph_launches_per_step": 1, "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
+def next_smooth7(n):
+    L = max(n, 2)
+    while True:
+        m = L
+        for q in (2, 3, 5, 7):
+            while m % q == 0:
+                m //= q
+        if m == 1:
+            return L
+        L += 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,10 +610,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--localsum", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the local sums of Eq. 2")
+    ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched"],
+                    help="order4: the default plain FP32 workload; the others time one form against it")
+    ap.add_argument("--crop-voxels", type=int, default=200)
+    ap.add_argument("--branches", type=int, default=4)
+    ap.add_argument("--plain-tomos", type=int, default=8)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "mixed":
+        run_mixed(args)
+    elif args.workload == "learned":
+        run_learned(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -283,6 +283,52 @@ def workload_order4(seed: int = 20240803, shape=(200, 512, 512), copies: int = 3
                          name="ttm_n4_512x512x200_t40")
 
 
+def workload_order6(seed: int = 20240804, shape=(256, 1024, 1024), copies: int = 2000) -> Workload:
+    """1024x1024x256 white noise, 48^3 template, r=19, order 6, 2000 copies
+    (as many as fit at 2r spacing) at SNR 0.05."""
+    return make_workload(shape, 48, 19.0, 6, copies, seed, snr=0.05, name="ttm_n6_1024x1024x256_t48")
+
+
+@dataclass
+class BatchWorkload:
+    tomos: list                  # float32 [Z][Y][X] arrays of uneven sizes
+    templates: list              # float32 [N][N][N]
+    mask_radius: float
+    order_n: int
+    copies: list                 # planted copies per tomogram
+    name: str = ""
+
+
+def workload_batched(seed: int = 20240805, n_tomos: int = 64, n_templates: int = 8, n_tmpl: int = 32,
+                     mask_radius: float = 12.0, lo: int = 96, hi: int = 256) -> BatchWorkload:
+    """n_tomos sub-tomograms, each axis uniform in [lo, hi], white noise with
+    20-80 planted copies each (the template of each copy drawn uniformly
+    from n_templates distinct n_tmpl^3 templates) at SNR 0.1; order 4."""
+    templates = [gaussian_blob_template(n_tmpl, seed, index=j) for j in range(n_templates)]
+    m = sphere_mask_values(n_tmpl, mask_radius)
+    amps = [math.sqrt(0.1 / float(np.var(t[m]))) for t in templates]
+    u = uniforms(seed, STREAM_MISC, 4 * n_tomos).reshape(n_tomos, 4)
+    tomos, copies = [], []
+    for i in range(n_tomos):
+        shape = tuple(int(lo + math.floor(u[i, a] * (hi - lo + 1))) for a in range(3))
+        count = int(20 + math.floor(u[i, 3] * 61))
+        s = seed * 1000 + i + 1
+        Z, Y, X = shape
+        vol = normals(s, STREAM_NOISE, Z * Y * X).reshape(shape)
+        centres = place_centres(shape, n_tmpl, count, 2.0 * mask_radius, s)
+        quats = shoemake_quats(uniforms(s, STREAM_ROT, 3 * len(centres)))
+        which = np.floor(uniforms(s, STREAM_PLACE, len(centres), offset=10 ** 6) * n_templates).astype(int)
+        for j in range(n_templates):
+            sel = which == j
+            if np.any(sel):
+                plant(vol, templates[j], centres[sel], quats[sel], amps[j])
+        tomos.append(vol.astype(np.float32))
+        copies.append(len(centres))
+    return BatchWorkload(tomos=tomos, templates=[t.astype(np.float32) for t in templates],
+                         mask_radius=mask_radius, order_n=4, copies=copies,
+                         name="ttm_n4_batched_%dx[%d-%d]^3_%dtmpl_t%d" % (n_tomos, lo, hi, n_templates, n_tmpl))
+
+
 def random_tensors(seed: int, count: int, K: int) -> np.ndarray:
     """count x K standard-normal tensor components (maximiser tests)."""
     return normals(seed, STREAM_MISC, count * K).reshape(count, K)

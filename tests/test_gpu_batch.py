@@ -193,16 +193,21 @@ def test_batch_replay_follows_input(T, ctx, batch_setup):
 
 
 def test_batch_vs_oracle(T, ctx, batch_setup):
+    """The oracle builds its own field from the same (float32) template and
+    works on the host copy of the same seeded tomogram."""
     p, tmpls, fields, tomos, B, outs = batch_setup
     r, n = 5.0, 4
+    ofield = {}
     for i, j, sc, ori, fr in outs[:4]:
         shape = SHAPES[i]
-        tomo = tomos[i].cpu().numpy().astype(np.float64)
+        tomo = synth.normals(30 + i, 1, int(np.prod(shape))).reshape(shape).astype(np.float32).astype(np.float64)
         pr = O.Prepared(tomo, tmpls[j].astype(np.float64), r)
+        if j not in ofield:
+            ofield[j] = O.tensor_field(pr.tp, O.rotation_set(16), n, 3)
         vox = O.valid_voxels(shape, tmpls[j].shape)
         vox = np.sort(np.random.default_rng(i + 10 * j).choice(vox, 300, replace=False))
         w, _, _ = O.local_w(pr.g, pr.m, vox, periodic=False, floor=pr.floor)
-        Cref = O.correlate(pr.g, fields[j].cpu().numpy(), vox, periodic=False, w=w)
+        Cref = O.correlate(pr.g, ofield[j], vox, periodic=False, w=w)
         sref, _, _ = O.maximise(Cref, n, 3, nsamples=20000)
         z, y, x = np.unravel_index(vox, shape)
         assert np.abs(sc.cpu().numpy()[z, y, x] - sref).max() <= S_TOL

@@ -135,7 +135,7 @@ def trained(T, ctx):
     torch.cuda.synchronize()
     fb = T.ttm_plan_fallback_count(M.plan)
     return dict(tmpl=tmpl, p=p, M=M, net=net, loss0=loss0, loss1=loss1, sl=sl, ol=ol, fl=fl, fb=fb, box=b,
-                centres=planted.centres)
+                centres=planted.centres, vol2=vol2)
 
 
 def test_training_reduces_loss(trained):
@@ -154,8 +154,9 @@ def test_learned_never_below_plain(trained):
 
 
 def test_learned_matches_oracle(trained):
-    """Scores within 1e-4 of the oracle at sampled valid voxels and at the
-    planted centres. The learned form may return any local maximum within
+    """Scores within 1e-4 of the oracle (its own field, normaliser and
+    direct-sum correlation) at sampled valid voxels and at the planted
+    centres. The learned form may return any local maximum within
     the score tolerance of the global one, so orientations are compared
     where the global maximum leads every other local maximum by more than
     that tolerance (and is not flat): at the planted centres and at the
@@ -169,15 +170,19 @@ def test_learned_matches_oracle(trained):
               if b[0] <= c[0] < b[1] and b[2] <= c[1] < b[3] and b[4] <= c[2] < b[5]]
     ci = np.array([(c[0] * shape[1] + c[1]) * shape[2] + c[2] for c in inside], dtype=np.int64)
     assert len(ci) >= 5
-    K = M.C.shape[0]
+    # the oracle's own pipeline: filter, mask, normalised template, field
+    # (same quadrature), local normaliser and direct-sum correlation
+    pr = O.Prepared(trained["vol2"].astype(np.float64), trained["tmpl"].astype(np.float64), R)
+    field = O.tensor_field(pr.tp, O.rotation_set(256), N, 3)
     for idx, min_well in ((vi, 500), (ci, len(ci) // 2)):
         t = dev(idx, torch.int64)
-        Cs = M.C.reshape(K, -1)[:, t].cpu().numpy().astype(np.float64)
+        w, _, _ = O.local_w(pr.g, pr.m, idx, periodic=False, floor=pr.floor)
+        Cs = O.correlate(pr.g, field, idx, periodic=False, w=w)
         so, uo, sec, curv = O.maximise(Cs, N, 3, 20000, with_curvature=True)
         sl = trained["sl"].flatten()[t].cpu().numpy()
         ul = trained["ol"].reshape(3, -1)[:, t].cpu().numpy().T
         assert np.abs(sl - so).max() <= S_TOL
-        F = trained["fl"].flatten()[t].cpu().numpy()
+        F = O.frobenius(Cs, N)
         well = ((so - sec) > S_TOL) & (curv > 1e-3 * F)
         ang = np.degrees(np.arccos(np.clip(np.abs(np.sum(ul * uo, 1)), 0, 1)))
         assert well.sum() >= min_well
