@@ -177,7 +177,13 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = synth.workload_order4()
+    if args.zyx:
+        # a smaller volume of the same workload (profiling captures): copies
+        # scale with the volume
+        shp = tuple(int(v) for v in args.zyx.split(","))
+        wl = synth.workload_order4(shape=shp, copies=max(1, int(300 * np.prod(shp) / (200 * 512 * 512))))
+    else:
+        wl = synth.workload_order4()
     Z, Y, X = wl.tomo.shape
     V = Z * Y * X
     n = wl.order_n
@@ -291,7 +297,8 @@ def run_ours(args, ws, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "shape_zyx": [Z, Y, X], "template": 40, "order_n": n,
+                "config": {"workload": WORKLOAD if not args.zyx else "ttm_n4_%dx%dx%d_t40" % (X, Y, Z),
+                           "shape_zyx": [Z, Y, X], "template": 40, "order_n": n,
                            "components": K, "mask_radius": wl.mask_radius, "rotations_field": 24 * 2048,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1gpu",
                            "local_sums": {"df64": "double-float (FP32 pairs, ~48-bit significand)",
@@ -612,6 +619,7 @@ def main():
                     help="arithmetic of the local sums of Eq. 2")
     ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched"],
                     help="order4: the default plain FP32 workload; the others time one form against it")
+    ap.add_argument("--zyx", default="", help="Z,Y,X of a smaller order-4 volume (profiling captures)")
     ap.add_argument("--crop-voxels", type=int, default=200)
     ap.add_argument("--branches", type=int, default=4)
     ap.add_argument("--plain-tomos", type=int, default=8)

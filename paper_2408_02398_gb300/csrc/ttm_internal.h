@@ -105,6 +105,8 @@ struct ttm_ctx {
     int num_sms = 0;
     ttm::DevBuf probe_tables;  // maximiser probe directions and monomials
     size_t probe_off[5] = {0, 0, 0, 0, 0};
+    ttm::DevBuf probe_half;    // FP16 monomial tables for the tensor-core probe product
+    size_t probe_half_off[3] = {0, 0, 0};
 };
 
 struct ttm_plan {

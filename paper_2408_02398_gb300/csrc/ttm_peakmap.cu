@@ -263,7 +263,22 @@ struct ProbeTables {
     const float* phi4;
     const float* phi6;
     const unsigned char* nbr;  // [kProbes][kProbeNbr] nearest probes (u ~ -u)
+    // FP16 copies [kProbes][pm_kxs(n)] (components beyond K and the row
+    // padding zero) for the tensor-core probe product
+    const __half* phi2h;
+    const __half* phi4h;
+    const __half* phi6h;
 };
+
+// probe values in shared memory: [kProbes][kPvStride] FP16; the row padding
+// keeps the fragment stores of a warp in distinct banks
+constexpr int kPvStride = kPmThreads + 8;
+__host__ __device__ constexpr int pm_kx(int n) { return (ncomp3(n) + 15) / 16 * 16; }
+__host__ __device__ constexpr int pm_kxs(int n) { return pm_kx(n) + 8; }
+__host__ __device__ constexpr size_t pm_smem_bytes(int n)
+{
+    return sizeof(__half) * ((size_t)kProbes * kPvStride + (size_t)kProbes * pm_kxs(n));
+}
 
 // which voxels a k_peakmap launch visits
 enum PmMode { PM_ALL = 0, PM_LIST = 1, PM_SWEEP = 2, PM_BOX = 3 };
@@ -285,7 +300,7 @@ struct PmGeom {
 };
 
 template <int N>
-__global__ void __launch_bounds__(kPmThreads)
+__global__ void __launch_bounds__(kPmThreads, N >= 6 ? 3 : 5)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
           float* __restrict__ frob, ProbeTables tabs, PmGeom geo)
 {
@@ -296,19 +311,26 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     const int64_t Vo = mode == PM_BOX ? geo.Vout : V;
     constexpr int K = ncomp3(N);
     constexpr int KP = kpad(N);
+    constexpr int KX = pm_kx(N);
+    constexpr int KXS = pm_kxs(N);
     constexpr int kStarts = nstarts(N);
     __shared__ float4 sdir[kProbes];
-    __shared__ __align__(16) float sphi[kProbes * KP];
     __shared__ unsigned char snbr[kProbes * kProbeNbr];
-    // [kProbes][kPmThreads] probe values, FP16 (only used to pick starts)
-    extern __shared__ __half pv[];
+    // pv: [kProbes][kPvStride] probe values / ||C||_F in FP16 (only used to
+    // pick starts); phih: [kProbes][KXS] FP16 weighted monomials
+    extern __shared__ __align__(16) __half pm_smem[];
+    __half* pv = pm_smem;
+    __half* phih = pm_smem + kProbes * kPvStride;
     {
-        const float* phi = N == 2 ? tabs.phi2 : (N == 4 ? tabs.phi4 : tabs.phi6);
-        for (int i = threadIdx.x; i < kProbes * KP; i += blockDim.x) sphi[i] = phi[i];
+        const __half* ph = N == 2 ? tabs.phi2h : (N == 4 ? tabs.phi4h : tabs.phi6h);
+        const uint4* src = reinterpret_cast<const uint4*>(ph);
+        uint4* dst = reinterpret_cast<uint4*>(phih);
+        for (int i = threadIdx.x; i < kProbes * KXS / 8; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < kProbes; i += blockDim.x) sdir[i] = tabs.dir[i];
         for (int i = threadIdx.x; i < kProbes * kProbeNbr; i += blockDim.x) snbr[i] = tabs.nbr[i];
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // persistent: each CTA walks voxel blocks with a grid stride
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t - threadIdx.x < n_items;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -342,35 +364,87 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
             for (int k2 = K; k2 < KP; k2++) c[k2] = 0.f;
         }
         const float F = sqrtf(F2);
-        // probe values to shared memory (one column per thread), and their max
+        // Probe values p_j / ||C||_F of the warp's 32 voxels on the tensor
+        // cores: x = C / ||C||_F (|x_k| <= 1) is staged in FP16 transposed
+        // into this warp's own columns of pv (rows = components), loaded as
+        // A fragments, and [32 voxels x KX] x [KX x 128 probes] runs as
+        // m16n8k16 products with FP32 accumulation; the results overwrite
+        // the same columns of pv in FP16, and each voxel's maximum reaches
+        // its thread by quad shuffles.
         float pmax = -INFINITY;
-#pragma unroll 2
-        for (int j = 0; j < kProbes; j++) {
-            const float4* ph = reinterpret_cast<const float4*>(sphi + j * KP);
-            float pj = 0.f;
+        {
+            const float invF = F > 0.f ? 1.f / F : 0.f;
 #pragma unroll
-            for (int q = 0; q < KP / 4; q++) {
-                const float4 f = ph[q];
-                pj += f.x * c[4 * q] + f.y * c[4 * q + 1] + f.z * c[4 * q + 2] + f.w * c[4 * q + 3];
+            for (int k = 0; k < KX; k++) pv[k * kPvStride + threadIdx.x] = __float2half_rn(k < K ? c[k] * invF : 0.f);
+            __syncwarp();
+            const int g = lane >> 2, t = lane & 3;
+            const int col0 = warp * 32 + g;
+            // one m-tile (16 voxels = 16 columns) at a time: its outputs
+            // overwrite only its own columns, so the other tile's staged
+            // rows stay intact
+#pragma unroll 1
+            for (int mt = 0; mt < 2; mt++) {
+                const int col = col0 + 16 * mt;
+                uint32_t a[KX / 16][4];
+#pragma unroll
+                for (int ks = 0; ks < KX / 16; ks++) {
+                    const int k0 = 16 * ks + 2 * t;
+                    auto pair = [&](int k, int cc) {
+                        __half2 h = __halves2half2(pv[k * kPvStride + cc], pv[(k + 1) * kPvStride + cc]);
+                        return *reinterpret_cast<uint32_t*>(&h);
+                    };
+                    a[ks][0] = pair(k0, col);
+                    a[ks][1] = pair(k0, col + 8);
+                    a[ks][2] = pair(k0 + 8, col);
+                    a[ks][3] = pair(k0 + 8, col + 8);
+                }
+                __syncwarp();
+                float mA = -INFINITY, mB = -INFINITY;
+#pragma unroll 2
+                for (int nt = 0; nt < kProbes / 8; nt++) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    const __half* br = phih + (nt * 8 + g) * KXS + 2 * t;
+#pragma unroll
+                    for (int ks = 0; ks < KX / 16; ks++)
+                        mma_f16(acc, a[ks], *reinterpret_cast<const uint32_t*>(br + 16 * ks),
+                                *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8));
+                    const int j0 = nt * 8 + 2 * t;
+                    pv[j0 * kPvStride + col] = __float2half_rn(acc[0]);
+                    pv[(j0 + 1) * kPvStride + col] = __float2half_rn(acc[1]);
+                    pv[j0 * kPvStride + col + 8] = __float2half_rn(acc[2]);
+                    pv[(j0 + 1) * kPvStride + col + 8] = __float2half_rn(acc[3]);
+                    mA = fmaxf(mA, fmaxf(acc[0], acc[1]));
+                    mB = fmaxf(mB, fmaxf(acc[2], acc[3]));
+                }
+                mA = fmaxf(mA, __shfl_xor_sync(0xffffffffu, mA, 1));
+                mA = fmaxf(mA, __shfl_xor_sync(0xffffffffu, mA, 2));
+                mB = fmaxf(mB, __shfl_xor_sync(0xffffffffu, mB, 1));
+                mB = fmaxf(mB, __shfl_xor_sync(0xffffffffu, mB, 2));
+                // lane 16 mt + r owns row r: rows 0..7 sit in quad r (c0, c1),
+                // rows 8..15 in quad r - 8 (c2, c3)
+                const int r = lane - 16 * mt;
+                const int src = 4 * (r & 7);
+                const float vA = __shfl_sync(0xffffffffu, mA, src);
+                const float vB = __shfl_sync(0xffffffffu, mB, src);
+                if (r >= 0 && r < 16) pmax = r < 8 ? vA : vB;
             }
-            pv[j * kPmThreads + threadIdx.x] = __float2half_rn(pj);
-            pmax = fmaxf(pmax, pj);
+            __syncwarp();
         }
         // starts: the best kStarts discrete local maxima (not below any of
         // their kProbeNbr nearest probes) within kStartMargin ||C||_F of the
-        // best probe, kept sorted in registers
-        const float thr = pmax - kStartMargin * F;
+        // best probe, kept sorted in registers (probe values are / ||C||_F)
+        const float thr = pmax - kStartMargin;
         float sv[kStarts];
         int sj[kStarts];
 #pragma unroll
         for (int s = 0; s < kStarts; s++) { sv[s] = -INFINITY; sj[s] = 0; }
         for (int j = 0; j < kProbes; j++) {
-            const float pj = __half2float(pv[j * kPmThreads + threadIdx.x]);
+            const float pj = __half2float(pv[j * kPvStride + threadIdx.x]);
             if (pj < thr || !(pj > sv[kStarts - 1])) continue;
             bool is_max = true;
 #pragma unroll
             for (int b = 0; b < kProbeNbr; b++)
-                if (__half2float(pv[snbr[j * kProbeNbr + b] * kPmThreads + threadIdx.x]) > pj) is_max = false;
+                if (__half2float(pv[snbr[j * kProbeNbr + b] * kPvStride + threadIdx.x]) > pj) is_max = false;
             if (!is_max) continue;
             float cv = pj;
             int cj = j;
@@ -626,6 +700,15 @@ void build_probe_tables(std::vector<float>& out, size_t off[5])
     std::memcpy(&out[off[4]], nb.data(), nb.size());
 }
 
+// FP16 copy of a weighted-monomial table: [kProbes][KP] FP32 -> [kProbes][KXS]
+__global__ void k_phi_half(const float* __restrict__ phi, int KP, int K, int KXS, __half* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kProbes * KXS; i += gridDim.x * blockDim.x) {
+        const int j = i / KXS, k = i - j * KXS;
+        out[i] = __float2half_rn(k < K ? phi[j * KP + k] : 0.f);
+    }
+}
+
 void upload_probe_tables(ttm_ctx* ctx)
 {
     std::vector<float> h;
@@ -634,14 +717,30 @@ void upload_probe_tables(ttm_ctx* ctx)
     ctx->probe_tables.alloc(h.size() * sizeof(float));
     TTM_CUDA_TRY(cudaMemcpy(ctx->probe_tables.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
     for (int i = 0; i < 5; i++) ctx->probe_off[i] = off[i];
+    size_t total = 0;
+    const int orders[3] = {2, 4, 6};
+    for (int q = 0; q < 3; q++) {
+        ctx->probe_half_off[q] = total;
+        total += (size_t)kProbes * pm_kxs(orders[q]);
+    }
+    ctx->probe_half.alloc(total * sizeof(__half));
+    for (int q = 0; q < 3; q++) {
+        const int n = orders[q];
+        k_phi_half<<<64, 256>>>(ctx->probe_tables.as<float>() + off[1 + q], kpad(n), ncomp3(n), pm_kxs(n),
+                                ctx->probe_half.as<__half>() + ctx->probe_half_off[q]);
+        TTM_LAUNCH_CHECK();
+    }
+    TTM_CUDA_TRY(cudaDeviceSynchronize());
 }
 
 static ProbeTables probe_tables(ttm_ctx* ctx)
 {
     const float* base = ctx->probe_tables.as<float>();
+    const __half* hb = ctx->probe_half.as<__half>();
     return ProbeTables{reinterpret_cast<const float4*>(base + ctx->probe_off[0]), base + ctx->probe_off[1],
                        base + ctx->probe_off[2], base + ctx->probe_off[3],
-                       reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4])};
+                       reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4]),
+                       hb + ctx->probe_half_off[0], hb + ctx->probe_half_off[1], hb + ctx->probe_half_off[2]};
 }
 
 // plain maximiser over all voxels (PM_ALL) or the learned path's fallbacks
@@ -651,7 +750,7 @@ static void plain_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* sco
     const ProbeTables t = probe_tables(ctx);
     const int64_t items = geo.mode == PM_BOX ? (int64_t)geo.bz * geo.by * geo.bx : V;
     const int64_t blocks = std::max<int64_t>(1, ceil_div(items, kPmThreads));
-    const size_t smem = (size_t)kProbes * kPmThreads * sizeof(__half);
+    const size_t smem = pm_smem_bytes(n);
     // enough CTAs to fill every SM several times, then a grid stride
     const int64_t grid = std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 32);
     // static tables + dynamic probe values can exceed the default 48 KB
