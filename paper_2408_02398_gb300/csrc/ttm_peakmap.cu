@@ -4,13 +4,13 @@
 //   p_x(u) = C(x) . u^{(x)n} = sum_alpha mult(alpha) C_alpha(x) u^alpha.
 //
 // One thread per voxel, components loaded structure-of-arrays (coalesced),
-// persistent CTAs. The form is evaluated at P fixed probe directions on the
-// half-sphere (p is even; the probe table sits in shared memory and is read
-// as broadcast float4s; probe values are kept in FP16, only to pick starts).
-// The probes that are not below any of their nearest probes (discrete local
-// maxima) and lie within 0.2 ||C||_F of the best probe are the candidate
-// basins; the best NS of them (2, 3, 4 for n = 2, 4, 6) get two interleaved
-// Newton steps each and the best of those is polished to convergence. The
+// persistent CTAs. The form is evaluated at P = 128 fixed probe directions on
+// the half-sphere (p is even) as a tensor-core product per warp; the probe
+// values are kept in FP16 in shared memory, only to pick starts. The starts
+// are the best probe and, by angular suppression, up to NS - 1 more (NS = 2
+// for n = 2, 3 otherwise): the best probe farther than 20 degrees from the
+// starts already taken, if within 0.2 ||C||_F of the best. Each start gets
+// two interleaved Newton steps and the best is polished to convergence. The
 // derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
 // matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
 // is a Riemannian Newton step in a Householder tangent basis, limited to
@@ -34,16 +34,18 @@ constexpr int kProbes = 128;
 constexpr int kPmThreads = 128;
 constexpr int kPreIters = 2;      // cheap polish of every start
 constexpr int kNewtonIters = 10;  // full polish of the best one
-constexpr int kProbeNbr = 6;
 // probes more than this fraction of ||C||_F below the best probe are not
 // considered as starts
 constexpr float kStartMargin = 0.2f;
+// extra starts lie farther than this from the starts already chosen
+constexpr double kStartSepDeg = 20.0;
+constexpr float kStartSepCos = 0.93969262f;  // cos(20 degrees)
 
 __host__ __device__ constexpr int ncomp3(int n) { return (n + 1) * (n + 2) / 2; }
 // starts polished per voxel: order 2 has a single maximum pair; higher
 // orders have more, narrower maxima (and the FP16 probe values can reorder
 // near-equal candidates)
-__host__ __device__ constexpr int nstarts(int n) { return n >= 6 ? 4 : (n >= 4 ? 3 : 2); }
+__host__ __device__ constexpr int nstarts(int n) { return n >= 4 ? 3 : 2; }
 __host__ __device__ constexpr int kpad(int n) { return (ncomp3(n) + 3) / 4 * 4; }
 __host__ __device__ constexpr float factf(int n) { return n <= 1 ? 1.f : n * factf(n - 1); }
 // position of exponents (a, b, n-a-b) in graded-lex descending order
@@ -262,7 +264,7 @@ struct ProbeTables {
     const float* phi2;
     const float* phi4;
     const float* phi6;
-    const unsigned char* nbr;  // [kProbes][kProbeNbr] nearest probes (u ~ -u)
+    const uint4* far;          // [kProbes] 128-bit rows: probes j with |d_i . d_j| < cos(kStartSepDeg)
     // FP16 copies [kProbes][pm_kxs(n)] (components beyond K and the row
     // padding zero) for the tensor-core probe product
     const __half* phi2h;
@@ -315,7 +317,6 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     constexpr int KXS = pm_kxs(N);
     constexpr int kStarts = nstarts(N);
     __shared__ float4 sdir[kProbes];
-    __shared__ unsigned char snbr[kProbes * kProbeNbr];
     // pv: [kProbes][kPvStride] probe values / ||C||_F in FP16 (only used to
     // pick starts); phih: [kProbes][KXS] FP16 weighted monomials
     extern __shared__ __align__(16) __half pm_smem[];
@@ -327,7 +328,6 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
         uint4* dst = reinterpret_cast<uint4*>(phih);
         for (int i = threadIdx.x; i < kProbes * KXS / 8; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < kProbes; i += blockDim.x) sdir[i] = tabs.dir[i];
-        for (int i = threadIdx.x; i < kProbes * kProbeNbr; i += blockDim.x) snbr[i] = tabs.nbr[i];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -372,6 +372,7 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
         // the same columns of pv in FP16, and each voxel's maximum reaches
         // its thread by quad shuffles.
         float pmax = -INFINITY;
+        int jmax = 0;
         {
             const float invF = F > 0.f ? 1.f / F : 0.f;
 #pragma unroll
@@ -400,6 +401,7 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                 }
                 __syncwarp();
                 float mA = -INFINITY, mB = -INFINITY;
+                int iA = 0, iB = 0;
 #pragma unroll 2
                 for (int nt = 0; nt < kProbes / 8; nt++) {
                     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -413,47 +415,68 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                     pv[(j0 + 1) * kPvStride + col] = __float2half_rn(acc[1]);
                     pv[j0 * kPvStride + col + 8] = __float2half_rn(acc[2]);
                     pv[(j0 + 1) * kPvStride + col + 8] = __float2half_rn(acc[3]);
-                    mA = fmaxf(mA, fmaxf(acc[0], acc[1]));
-                    mB = fmaxf(mB, fmaxf(acc[2], acc[3]));
+                    // running maximum and its probe (lowest index on ties)
+                    if (acc[0] > mA) { mA = acc[0]; iA = j0; }
+                    if (acc[1] > mA) { mA = acc[1]; iA = j0 + 1; }
+                    if (acc[2] > mB) { mB = acc[2]; iB = j0; }
+                    if (acc[3] > mB) { mB = acc[3]; iB = j0 + 1; }
                 }
-                mA = fmaxf(mA, __shfl_xor_sync(0xffffffffu, mA, 1));
-                mA = fmaxf(mA, __shfl_xor_sync(0xffffffffu, mA, 2));
-                mB = fmaxf(mB, __shfl_xor_sync(0xffffffffu, mB, 1));
-                mB = fmaxf(mB, __shfl_xor_sync(0xffffffffu, mB, 2));
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    const float oA = __shfl_xor_sync(0xffffffffu, mA, o), oB = __shfl_xor_sync(0xffffffffu, mB, o);
+                    const int jA = __shfl_xor_sync(0xffffffffu, iA, o), jB = __shfl_xor_sync(0xffffffffu, iB, o);
+                    if (oA > mA || (oA == mA && jA < iA)) { mA = oA; iA = jA; }
+                    if (oB > mB || (oB == mB && jB < iB)) { mB = oB; iB = jB; }
+                }
                 // lane 16 mt + r owns row r: rows 0..7 sit in quad r (c0, c1),
                 // rows 8..15 in quad r - 8 (c2, c3)
                 const int r = lane - 16 * mt;
                 const int src = 4 * (r & 7);
                 const float vA = __shfl_sync(0xffffffffu, mA, src);
                 const float vB = __shfl_sync(0xffffffffu, mB, src);
-                if (r >= 0 && r < 16) pmax = r < 8 ? vA : vB;
+                const int kA = __shfl_sync(0xffffffffu, iA, src);
+                const int kB = __shfl_sync(0xffffffffu, iB, src);
+                if (r >= 0 && r < 16) {
+                    pmax = r < 8 ? vA : vB;
+                    jmax = r < 8 ? kA : kB;
+                }
             }
             __syncwarp();
         }
-        // starts: the best kStarts discrete local maxima (not below any of
-        // their kProbeNbr nearest probes) within kStartMargin ||C||_F of the
-        // best probe, kept sorted in registers (probe values are / ||C||_F)
+        // Starts by angular suppression: the best probe, then the best probe
+        // farther than kStartSepDeg from it, then the best one farther than
+        // that from both, each only if within kStartMargin ||C||_F of the best.
+        // Each extra start is one branch-free pass over the FP16 probe values
+        // masked by a precomputed 128-bit row of "far" probes.
         const float thr = pmax - kStartMargin;
         float sv[kStarts];
         int sj[kStarts];
 #pragma unroll
         for (int s = 0; s < kStarts; s++) { sv[s] = -INFINITY; sj[s] = 0; }
-        for (int j = 0; j < kProbes; j++) {
-            const float pj = __half2float(pv[j * kPvStride + threadIdx.x]);
-            if (pj < thr || !(pj > sv[kStarts - 1])) continue;
-            bool is_max = true;
+        sv[0] = pmax;
+        sj[0] = jmax;
+        {
+            uint4 far = __ldg(tabs.far + jmax);
 #pragma unroll
-            for (int b = 0; b < kProbeNbr; b++)
-                if (__half2float(pv[snbr[j * kProbeNbr + b] * kPvStride + threadIdx.x]) > pj) is_max = false;
-            if (!is_max) continue;
-            float cv = pj;
-            int cj = j;
+            for (int s = 1; s < kStarts; s++) {
+                const uint32_t fw[4] = {far.x, far.y, far.z, far.w};
+                float bv = -INFINITY;
+                int bj = 0;
 #pragma unroll
-            for (int s = 0; s < kStarts; s++) {
-                if (cv > sv[s]) {
-                    const float tv = sv[s]; const int tj = sj[s];
-                    sv[s] = cv; sj[s] = cj;
-                    cv = tv; cj = tj;
+                for (int w = 0; w < kProbes / 32; w++) {
+#pragma unroll 8
+                    for (int bb = 0; bb < 32; bb++) {
+                        const float v = __half2float(pv[(32 * w + bb) * kPvStride + threadIdx.x]);
+                        if (((fw[w] >> bb) & 1u) && v > bv) { bv = v; bj = 32 * w + bb; }
+                    }
+                }
+                if (bv >= thr) {
+                    sv[s] = bv;
+                    sj[s] = bj;
+                    const uint4 f2 = __ldg(tabs.far + bj);
+                    far.x &= f2.x; far.y &= f2.y; far.z &= f2.z; far.w &= f2.w;
+                } else {
+                    break;
                 }
             }
         }
@@ -503,21 +526,33 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
 
 // Learned maximiser: the MLP (BF16 tensor cores) predicts the maximising
 // direction from C / ||C||_F and Newton polishes it. The plain maximiser's
-// probe values (FP32, the same kProbes directions) then serve as the check:
-// where the polished value falls below the best probe, a second polish
-// starts from that probe and the better of the two is kept. A voxel is
-// accepted when its kept polish converged and its value is not below the
-// best probe; the others are appended to `list` (warp-aggregated atomics)
-// for the plain maximiser, and past the list's capacity their score is set
-// to NaN for a sweep instead.
+// probe directions then serve as the check. Their values come from the
+// same FP16 tensor-core product as in the plain maximiser (best, its index,
+// runner-up); with |x_k| <= 1 and sum mult x^2 = 1, Cauchy-Schwarz bounds
+// every FP16 probe value's error by kProbeErr ||C||_F, so every probe is
+// below B = max(p(best probe) in FP32, (runner-up + kProbeErr) ||C||_F).
+// Where the polished value is below B, a second polish starts from the best
+// probe and the better of the two is kept. A voxel is accepted when its
+// kept polish converged, its value is not below B (up to 1e-5 ||C||_F), the
+// plain maximiser would start from the best probe alone (a second sweep of
+// the probe product finds no probe farther than kStartSepDeg from it within
+// kStartMargin, by the same FP16 values and test) and the polished direction
+// lies within kStartSepDeg of that probe; the others are appended to `list`
+// (warp-aggregated atomics) for the plain maximiser, and past the list's
+// capacity their score is set to NaN for a sweep instead.
 constexpr int kMlThreads = 256;
 constexpr int kMlWarps = kMlThreads / 32;
+
+// bound on |FP16 probe value - exact| / ||C||_F: two FP16 roundings of the
+// operands (2 * 2^-11 on a sum of |phi x| <= 1) plus subnormal inputs and
+// FP32 accumulation, with margin
+constexpr float kProbeErr = 1.5e-3f;
 
 template <int N>
 __host__ __device__ constexpr size_t ml_smem_bytes()
 {
     return kMlpImageBytes + sizeof(__nv_bfloat16) * kMlWarps * 32 * kW1S + sizeof(float) * kMlWarps * 32 * 4 +
-           sizeof(float) * kProbes * kpad(N) + sizeof(float4) * kProbes;
+           sizeof(__half) * kProbes * pm_kxs(N) + sizeof(float4) * kProbes;
 }
 
 template <int N>
@@ -529,6 +564,7 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
     constexpr int K = ncomp3(N);
     constexpr int KP = kpad(N);
     constexpr int KX = mlp_kx(K);
+    constexpr int KXS = pm_kxs(N);
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* img = smem;
     size_t off = kMlpImageBytes;
@@ -536,16 +572,19 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
     off += sizeof(__nv_bfloat16) * kMlWarps * 32 * kW1S;
     float* sy = reinterpret_cast<float*>(smem + off) + (threadIdx.x >> 5) * 32 * 4;
     off += sizeof(float) * kMlWarps * 32 * 4;
-    float* sphi = reinterpret_cast<float*>(smem + off);
-    off += sizeof(float) * kProbes * KP;
+    __half* phih = reinterpret_cast<__half*>(smem + off);
+    off += sizeof(__half) * kProbes * KXS;
     float4* sdir = reinterpret_cast<float4*>(smem + off);
     mlp_image_to_smem(image, img);
     {
-        const float* phi = N == 2 ? tabs.phi2 : (N == 4 ? tabs.phi4 : tabs.phi6);
-        for (int i = threadIdx.x; i < kProbes * KP; i += blockDim.x) sphi[i] = phi[i];
+        const __half* ph = N == 2 ? tabs.phi2h : (N == 4 ? tabs.phi4h : tabs.phi6h);
+        const uint4* src = reinterpret_cast<const uint4*>(ph);
+        uint4* dst = reinterpret_cast<uint4*>(phih);
+        for (int i = threadIdx.x; i < kProbes * KXS / 8; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < kProbes; i += blockDim.x) sdir[i] = tabs.dir[i];
     }
     __syncthreads();
+    const float* phi32 = N == 2 ? tabs.phi2 : (N == 4 ? tabs.phi4 : tabs.phi6);
     const float* b3 = reinterpret_cast<const float*>(img + kMlpOffB3);
     const int lane = threadIdx.x & 31;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - threadIdx.x < V;
@@ -570,6 +609,98 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
         }
         const float F = sqrtf(F2);
         const float inv = F > 0.f ? 1.f / F : 0.f;
+        // probe values / ||C||_F on the tensor cores: x in FP16 in the staging
+        // rows, m16n8k16 with the FP16 probe table, FP32 accumulation; only
+        // the best value, its probe and the runner-up are kept
+        float pm1 = -INFINITY, pm2 = -INFINITY, pfar = -INFINITY;
+        int pj1 = 0;
+        {
+            __half* hx = reinterpret_cast<__half*>(sx);
+#pragma unroll
+            for (int k = 0; k < KX; k += 2)
+                *reinterpret_cast<__half2*>(hx + lane * kW1S + k) =
+                    __floats2half2_rn(k < K ? c[k] * inv : 0.f, k + 1 < K ? c[k + 1] * inv : 0.f);
+            __syncwarp();
+            const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+            for (int mt = 0; mt < 2; mt++) {
+                const __half* r0 = hx + (16 * mt + g) * kW1S + 2 * t;
+                const __half* r1 = r0 + 8 * kW1S;
+                uint32_t a[KX / 16][4];
+#pragma unroll
+                for (int ks = 0; ks < KX / 16; ks++) {
+                    a[ks][0] = *reinterpret_cast<const uint32_t*>(r0 + 16 * ks);
+                    a[ks][1] = *reinterpret_cast<const uint32_t*>(r1 + 16 * ks);
+                    a[ks][2] = *reinterpret_cast<const uint32_t*>(r0 + 16 * ks + 8);
+                    a[ks][3] = *reinterpret_cast<const uint32_t*>(r1 + 16 * ks + 8);
+                }
+                float aM = -INFINITY, aS = -INFINITY, bM = -INFINITY, bS = -INFINITY;
+                int aI = 0, bI = 0;
+                auto upd = [](float v, int j, float& M, float& S, int& I) {
+                    if (v > M) { S = M; M = v; I = j; }
+                    else if (v > S) S = v;
+                };
+#pragma unroll 2
+                for (int nt = 0; nt < kProbes / 8; nt++) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    const __half* br = phih + (nt * 8 + g) * KXS + 2 * t;
+#pragma unroll
+                    for (int ks = 0; ks < KX / 16; ks++)
+                        mma_f16(acc, a[ks], *reinterpret_cast<const uint32_t*>(br + 16 * ks),
+                                *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8));
+                    const int j0 = nt * 8 + 2 * t;
+                    upd(acc[0], j0, aM, aS, aI);
+                    upd(acc[1], j0 + 1, aM, aS, aI);
+                    upd(acc[2], j0, bM, bS, bI);
+                    upd(acc[3], j0 + 1, bM, bS, bI);
+                }
+                auto merge = [](float& M, float& S, int& I, float oM, float oS, int oI) {
+                    if (oM > M || (oM == M && oI < I)) { S = fmaxf(M, fmaxf(S, oS)); M = oM; I = oI; }
+                    else S = fmaxf(oM, fmaxf(S, oS));
+                };
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    merge(aM, aS, aI, __shfl_xor_sync(0xffffffffu, aM, o), __shfl_xor_sync(0xffffffffu, aS, o),
+                          __shfl_xor_sync(0xffffffffu, aI, o));
+                    merge(bM, bS, bI, __shfl_xor_sync(0xffffffffu, bM, o), __shfl_xor_sync(0xffffffffu, bS, o),
+                          __shfl_xor_sync(0xffffffffu, bI, o));
+                }
+                // second sweep: the best FP16-rounded value among the probes
+                // farther than kStartSepDeg from each row's best probe (the
+                // plain maximiser's test for a second start)
+                const uint4 fa = __ldg(tabs.far + aI), fb = __ldg(tabs.far + bI);
+                const uint32_t fwa[4] = {fa.x, fa.y, fa.z, fa.w}, fwb[4] = {fb.x, fb.y, fb.z, fb.w};
+                float aF = -INFINITY, bF = -INFINITY;
+#pragma unroll
+                for (int nt = 0; nt < kProbes / 8; nt++) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    const __half* br = phih + (nt * 8 + g) * KXS + 2 * t;
+#pragma unroll
+                    for (int ks = 0; ks < KX / 16; ks++)
+                        mma_f16(acc, a[ks], *reinterpret_cast<const uint32_t*>(br + 16 * ks),
+                                *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8));
+                    const int j0 = nt * 8 + 2 * t;
+                    const uint32_t wa = fwa[nt >> 2] >> (j0 & 31), wb = fwb[nt >> 2] >> (j0 & 31);
+                    if (wa & 1u) aF = fmaxf(aF, __half2float(__float2half_rn(acc[0])));
+                    if (wa & 2u) aF = fmaxf(aF, __half2float(__float2half_rn(acc[1])));
+                    if (wb & 1u) bF = fmaxf(bF, __half2float(__float2half_rn(acc[2])));
+                    if (wb & 2u) bF = fmaxf(bF, __half2float(__float2half_rn(acc[3])));
+                }
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    aF = fmaxf(aF, __shfl_xor_sync(0xffffffffu, aF, o));
+                    bF = fmaxf(bF, __shfl_xor_sync(0xffffffffu, bF, o));
+                }
+                const int r = lane - 16 * mt;
+                const int src = 4 * (r & 7);
+                const float vM = __shfl_sync(0xffffffffu, r < 8 ? aM : bM, src);
+                const float vS = __shfl_sync(0xffffffffu, r < 8 ? aS : bS, src);
+                const int vI = __shfl_sync(0xffffffffu, r < 8 ? aI : bI, src);
+                const float vF = __shfl_sync(0xffffffffu, r < 8 ? aF : bF, src);
+                if (r >= 0 && r < 16) { pm1 = vM; pm2 = vS; pj1 = vI; pfar = vF; }
+            }
+            __syncwarp();
+        }
         // MLP input row (C / ||C||_F in BF16, zero padded to KX columns)
 #pragma unroll
         for (int k = 0; k < KX; k += 2) {
@@ -590,29 +721,35 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
             float A[6];
             best = form_at<N>(c, ux, uy, uz, A);
             bool conv = polish<N, kNewtonIters>(c, F, ux, uy, uz, best, A);
-            // best probe, FP32
-            float pm = -INFINITY;
-            int jm = 0;
-#pragma unroll 2
-            for (int j = 0; j < kProbes; j++) {
-                const float4* ph = reinterpret_cast<const float4*>(sphi + j * KP);
-                float pj = 0.f;
+            // bound on every probe value: the best probe in FP32, the others
+            // by the runner-up plus the FP16 error bound
+            float pexact = 0.f;
+            {
+                const float4* ph = reinterpret_cast<const float4*>(phi32 + pj1 * KP);
 #pragma unroll
                 for (int q = 0; q < KP / 4; q++) {
-                    const float4 f = ph[q];
-                    pj += f.x * c[4 * q] + f.y * c[4 * q + 1] + f.z * c[4 * q + 2] + f.w * c[4 * q + 3];
+                    const float4 f = __ldg(ph + q);
+                    pexact += f.x * c[4 * q] + f.y * c[4 * q + 1] + f.z * c[4 * q + 2] + f.w * c[4 * q + 3];
                 }
-                if (pj > pm) { pm = pj; jm = j; }
             }
+            const float pm = fmaxf(pexact, (pm2 + kProbeErr) * F);
             const float tol = 1e-5f * F;
             if (!(conv && best >= pm - tol)) {
-                const float4 d = sdir[jm];
+                const float4 d = sdir[pj1];
                 float vx = d.x, vy = d.y, vz = d.z, A2[6];
                 float p2 = form_at<N>(c, vx, vy, vz, A2);
                 const bool conv2 = polish<N, kNewtonIters>(c, F, vx, vy, vz, p2, A2);
                 if (p2 > best) { best = p2; ux = vx; uy = vy; uz = vz; conv = conv2; }
             }
-            accept = conv && best >= pm - tol;
+            // accepted only where the plain maximiser would itself use the
+            // best probe as its single start (no far probe within the margin)
+            // and the polished direction lies in that probe's region, so the
+            // two forms end at the same maximum; elsewhere the plain
+            // maximiser decides
+            const float4 dj = sdir[pj1];
+            const bool single = !(pfar >= pm1 - kStartMargin);
+            const bool aligned = fabsf(ux * dj.x + uy * dj.y + uz * dj.z) >= kStartSepCos;
+            accept = conv && best >= pm - tol && single && aligned;
         } else {
             ux = 0.f; uy = 0.f; uz = 1.f;
         }
@@ -678,26 +815,18 @@ void build_probe_tables(std::vector<float>& out, size_t off[5])
             (void)K;
         }
     }
-    // nearest kProbeNbr probes of every probe, packed 4 per float slot
+    // "far" rows: bit j of row i is set when |d_i . d_j| < cos(kStartSepDeg)
+    // (u and -u are the same direction), 4 words per probe
     off[4] = out.size();
-    std::vector<unsigned char> nb(kProbes * kProbeNbr);
-    for (int i = 0; i < kProbes; i++) {
-        double bd[kProbeNbr];
-        int bi[kProbeNbr], m = 0;
+    const double cmax = std::cos(kStartSepDeg * M_PI / 180.0);
+    std::vector<uint32_t> far(kProbes * 4, 0u);
+    for (int i = 0; i < kProbes; i++)
         for (int j = 0; j < kProbes; j++) {
-            if (j == i) continue;
-            double dot = std::fabs(d[3 * i] * d[3 * j] + d[3 * i + 1] * d[3 * j + 1] + d[3 * i + 2] * d[3 * j + 2]);
-            if (m == kProbeNbr && dot <= bd[kProbeNbr - 1]) continue;
-            int pos = m < kProbeNbr ? m++ : kProbeNbr - 1;
-            while (pos > 0 && bd[pos - 1] < dot) { bd[pos] = bd[pos - 1]; bi[pos] = bi[pos - 1]; pos--; }
-            bd[pos] = dot;
-            bi[pos] = j;
+            const double dot = std::fabs(d[3 * i] * d[3 * j] + d[3 * i + 1] * d[3 * j + 1] + d[3 * i + 2] * d[3 * j + 2]);
+            if (dot < cmax) far[i * 4 + j / 32] |= 1u << (j % 32);
         }
-        for (int b = 0; b < kProbeNbr; b++) nb[i * kProbeNbr + b] = (unsigned char)bi[b];
-    }
-    const size_t nfl = (nb.size() + 3) / 4;
-    out.resize(out.size() + nfl, 0.f);
-    std::memcpy(&out[off[4]], nb.data(), nb.size());
+    out.resize(out.size() + far.size(), 0.f);
+    std::memcpy(&out[off[4]], far.data(), far.size() * sizeof(uint32_t));
 }
 
 // FP16 copy of a weighted-monomial table: [kProbes][KP] FP32 -> [kProbes][KXS]
@@ -739,7 +868,7 @@ static ProbeTables probe_tables(ttm_ctx* ctx)
     const __half* hb = ctx->probe_half.as<__half>();
     return ProbeTables{reinterpret_cast<const float4*>(base + ctx->probe_off[0]), base + ctx->probe_off[1],
                        base + ctx->probe_off[2], base + ctx->probe_off[3],
-                       reinterpret_cast<const unsigned char*>(base + ctx->probe_off[4]),
+                       reinterpret_cast<const uint4*>(base + ctx->probe_off[4]),
                        hb + ctx->probe_half_off[0], hb + ctx->probe_half_off[1], hb + ctx->probe_half_off[2]};
 }
 
