@@ -272,14 +272,16 @@ struct ProbeTables {
     const __half* phi6h;
 };
 
-// probe values in shared memory: [kProbes][kPvStride] FP16; the row padding
-// keeps the fragment stores of a warp in distinct banks
+// probe values in shared memory as FP16 pairs: row p holds probes (2p, 2p+1)
+// of every thread's voxel, one 32-bit word per thread; the padding (136
+// words per row) keeps the fragment stores and loads of a warp in distinct
+// banks
 constexpr int kPvStride = kPmThreads + 8;
 __host__ __device__ constexpr int pm_kx(int n) { return (ncomp3(n) + 15) / 16 * 16; }
 __host__ __device__ constexpr int pm_kxs(int n) { return pm_kx(n) + 8; }
 __host__ __device__ constexpr size_t pm_smem_bytes(int n)
 {
-    return sizeof(__half) * ((size_t)kProbes * kPvStride + (size_t)kProbes * pm_kxs(n));
+    return sizeof(__half2) * (size_t)(kProbes / 2) * kPvStride + sizeof(__half) * (size_t)kProbes * pm_kxs(n);
 }
 
 // which voxels a k_peakmap launch visits
@@ -320,7 +322,7 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     // pv: [kProbes][kPvStride] probe values / ||C||_F in FP16 (only used to
     // pick starts); phih: [kProbes][KXS] FP16 weighted monomials
     extern __shared__ __align__(16) __half pm_smem[];
-    __half* pv = pm_smem;
+    __half2* pv = reinterpret_cast<__half2*>(pm_smem);
     __half* phih = pm_smem + kProbes * kPvStride;
     {
         const __half* ph = N == 2 ? tabs.phi2h : (N == 4 ? tabs.phi4h : tabs.phi6h);
@@ -376,7 +378,9 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
         {
             const float invF = F > 0.f ? 1.f / F : 0.f;
 #pragma unroll
-            for (int k = 0; k < KX; k++) pv[k * kPvStride + threadIdx.x] = __float2half_rn(k < K ? c[k] * invF : 0.f);
+            for (int k = 0; k < KX; k += 2)
+                pv[(k / 2) * kPvStride + threadIdx.x] =
+                    __floats2half2_rn(k < K ? c[k] * invF : 0.f, k + 1 < K ? c[k + 1] * invF : 0.f);
             __syncwarp();
             const int g = lane >> 2, t = lane & 3;
             const int col0 = warp * 32 + g;
@@ -389,15 +393,11 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                 uint32_t a[KX / 16][4];
 #pragma unroll
                 for (int ks = 0; ks < KX / 16; ks++) {
-                    const int k0 = 16 * ks + 2 * t;
-                    auto pair = [&](int k, int cc) {
-                        __half2 h = __halves2half2(pv[k * kPvStride + cc], pv[(k + 1) * kPvStride + cc]);
-                        return *reinterpret_cast<uint32_t*>(&h);
-                    };
-                    a[ks][0] = pair(k0, col);
-                    a[ks][1] = pair(k0, col + 8);
-                    a[ks][2] = pair(k0 + 8, col);
-                    a[ks][3] = pair(k0 + 8, col + 8);
+                    const __half2* r = pv + (8 * ks + t) * kPvStride + col;
+                    a[ks][0] = *reinterpret_cast<const uint32_t*>(r);
+                    a[ks][1] = *reinterpret_cast<const uint32_t*>(r + 8);
+                    a[ks][2] = *reinterpret_cast<const uint32_t*>(r + 4 * kPvStride);
+                    a[ks][3] = *reinterpret_cast<const uint32_t*>(r + 4 * kPvStride + 8);
                 }
                 __syncwarp();
                 float mA = -INFINITY, mB = -INFINITY;
@@ -411,10 +411,8 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                         mma_f16(acc, a[ks], *reinterpret_cast<const uint32_t*>(br + 16 * ks),
                                 *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8));
                     const int j0 = nt * 8 + 2 * t;
-                    pv[j0 * kPvStride + col] = __float2half_rn(acc[0]);
-                    pv[(j0 + 1) * kPvStride + col] = __float2half_rn(acc[1]);
-                    pv[j0 * kPvStride + col + 8] = __float2half_rn(acc[2]);
-                    pv[(j0 + 1) * kPvStride + col + 8] = __float2half_rn(acc[3]);
+                    pv[(j0 / 2) * kPvStride + col] = __floats2half2_rn(acc[0], acc[1]);
+                    pv[(j0 / 2) * kPvStride + col + 8] = __floats2half2_rn(acc[2], acc[3]);
                     // running maximum and its probe (lowest index on ties)
                     if (acc[0] > mA) { mA = acc[0]; iA = j0; }
                     if (acc[1] > mA) { mA = acc[1]; iA = j0 + 1; }
@@ -464,10 +462,11 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                 int bj = 0;
 #pragma unroll
                 for (int w = 0; w < kProbes / 32; w++) {
-#pragma unroll 8
-                    for (int bb = 0; bb < 32; bb++) {
-                        const float v = __half2float(pv[(32 * w + bb) * kPvStride + threadIdx.x]);
-                        if (((fw[w] >> bb) & 1u) && v > bv) { bv = v; bj = 32 * w + bb; }
+#pragma unroll 4
+                    for (int bb = 0; bb < 32; bb += 2) {
+                        const float2 v = __half22float2(pv[(16 * w + bb / 2) * kPvStride + threadIdx.x]);
+                        if (((fw[w] >> bb) & 1u) && v.x > bv) { bv = v.x; bj = 32 * w + bb; }
+                        if (((fw[w] >> bb) & 2u) && v.y > bv) { bv = v.y; bj = 32 * w + bb + 1; }
                     }
                 }
                 if (bv >= thr) {
