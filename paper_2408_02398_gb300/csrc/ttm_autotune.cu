@@ -170,6 +170,12 @@ std::vector<int> length_candidates(int n)
 LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind)
 {
     LenPlan pl = make_len_plan(ctx->twiddles, L, kind);
+    // Double-float passes use the shared-memory Stockham kernels: the
+    // register four-step holds E complex double-float values per thread
+    // (168 registers and 78 KB of shared memory per CTA at L = 512, so 8
+    // warps per SM) and was measured slower (local sums of a 512x512x200
+    // tomogram 9.97 ms against 7.97 ms).
+    if (kind == TW_DF64) pl.no_reg = 1;
     if (kind != TW_F32) return pl;
     const TuneRec* r = find_rec(ctx, L);
     if (!r) return pl;

@@ -77,6 +77,7 @@ void autotune_shape(ttm_ctx* ctx, const int t[3], int out[3]);
 
 // LenPlan of length L and twiddle kind: the autotuned schedule and tile
 // width when the context has one for FP32 L, else the default schedule
+// (double-float lengths: always the shared-memory passes)
 LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind);
 
 // host mask on the template grid (Sec. 2 after Eq. 3); returns M

@@ -260,9 +260,9 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Zt, int Yt, int Xt, int Z, int Y, in
     p.px64 = make_len_plan(ctx->twiddles, X, TW_F64);
     p.py64 = make_len_plan(ctx->twiddles, Y, TW_F64);
     p.pz64 = make_len_plan(ctx->twiddles, Z, TW_F64);
-    p.pxd = make_len_plan(ctx->twiddles, X, TW_DF64);
-    p.pyd = make_len_plan(ctx->twiddles, Y, TW_DF64);
-    p.pzd = make_len_plan(ctx->twiddles, Z, TW_DF64);
+    p.pxd = ctx_len_plan(ctx, X, TW_DF64);
+    p.pyd = ctx_len_plan(ctx, Y, TW_DF64);
+    p.pzd = ctx_len_plan(ctx, Z, TW_DF64);
     const int64_t V = (int64_t)Z * Y * X, Vh = (int64_t)Z * Y * p.Xh;
     p.nblk_pre = ceil_div(V, kPreThreads);
     p.g32.alloc(V * sizeof(float));
