@@ -613,7 +613,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-voxels", type=int, default=60000)
+    ap.add_argument("--cpu-voxels", type=int, default=250000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--localsum", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the local sums of Eq. 2")
