@@ -126,7 +126,9 @@ ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, int tz, int
 /* A plan binds a tensor field to one tomogram shape: it holds the template
  * spectra (transformed along x and y, kept on the template's z rows), the
  * spectrum of the mask, and the per-tomogram workspace. Allocates device
- * memory (~ (K + 6) * Z*Y*(X/2+1) * 8 bytes for FP32). Blocking.
+ * memory (~ (K + 6) * Z*Y*(X/2+1) * 8 bytes for FP32). Blocking; the first
+ * plan of a context with a new extent also times the double-float
+ * transform kernels for it (a few milliseconds, kept in the context).
  *   precision  TTM_PREC_FP32, or TTM_PREC_FP16_SPECTRA / _BF16_SPECTRA:
  *              the template spectra and the K-component work buffer are
  *              stored as 16-bit pairs (half the bytes), each component
@@ -323,7 +325,9 @@ ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int Y, int X, 
 ttm_status ttm_autotune_shape(ttm_ctx* ctx, int Z, int Y, int X, int* zyx);
 /* Number of tuned lengths held by the context. */
 int ttm_autotune_entries(const ttm_ctx* ctx);
-/* Tuned records as JSON (one object per line: L, reg, W, rad, us_line);
+/* Tuned records as JSON (one object per line: L, kind (0 FP32, 2 double-
+ * float), reg, W, rad, us_line); double-float lengths are tuned (register
+ * against shared-memory pass) on their first use by a plan of the context;
  * load replaces records of the same length and rejects malformed files
  * with TTM_E_INVALID_ARG. */
 ttm_status ttm_autotune_save(const ttm_ctx* ctx, const char* path);

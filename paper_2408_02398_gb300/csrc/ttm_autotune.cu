@@ -83,11 +83,83 @@ double time_pass(float2* buf, const LenPlan& pl, cudaStream_t st, cudaEvent_t e0
     return 1000.0 * ms / reps / kTuneLines;
 }
 
-const TuneRec* find_rec(const ttm_ctx* ctx, int L)
+const TuneRec* find_rec(const ttm_ctx* ctx, int L, int kind = TW_F32)
 {
     for (const auto& r : ctx->tune)
-        if (r.L == L) return &r;
+        if (r.L == L && r.kind == kind) return &r;
     return nullptr;
+}
+
+// Double-float passes: the register four-step against the shared-memory
+// Stockham pass (default schedule and tile), timed on a strided pass over a
+// buffer of at least 256 MB, so that it runs from DRAM as the local sums do
+// (from L2 the register kernel's low occupancy hides and it wins where it
+// loses in place). Register pressure and shared memory per CTA differ a lot
+// with the length (32 double-float complex values per thread at 512 and
+// 1024), and the faster one was measured to change with it.
+int tune_lines_df(int L)
+{
+    const int64_t want = ((int64_t)1 << 28) / ((int64_t)L * (int64_t)sizeof(dcx));
+    return (int)std::max<int64_t>(4096, (want + 1023) / 1024 * 1024);
+}
+
+double time_pass_df(dcx* buf, int lines, const LenPlan& pl, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
+{
+    const StridedAxis ax{lines, 1, 0, lines};
+    auto run = [&]() {
+        launch_strided_any<df64, -1>(buf, ax, pl, ProIdentity<df64>(), StoreTo<df64>{buf, 0, lines}, st);
+    };
+    for (int i = 0; i < 2; i++) run();
+    TTM_CUDA_TRY(cudaEventRecord(e0, st));
+    const int reps = 4;
+    for (int i = 0; i < reps; i++) run();
+    TTM_CUDA_TRY(cudaEventRecord(e1, st));
+    TTM_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TTM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    return 1000.0 * ms / reps / lines;
+}
+
+const TuneRec& tune_length_df(ttm_ctx* ctx, int L)
+{
+    if (const TuneRec* r = find_rec(ctx, L, TW_DF64)) return *r;
+    TuneRec rec;
+    rec.L = L;
+    rec.kind = TW_DF64;
+    LenPlan base = make_len_plan(ctx->twiddles, L, TW_DF64);
+    rec.nst = base.nst;
+    std::copy(base.rad, base.rad + base.nst, rec.rad);
+    int E, P;
+    if (fs_split(L, E, P)) {
+        const int lines = tune_lines_df(L);
+        DevBuf buf;
+        buf.alloc((size_t)L * lines * sizeof(dcx));
+        TTM_CUDA_TRY(cudaMemset(buf.p, 0, buf.bytes));
+        cudaStream_t st;
+        cudaEvent_t e0, e1;
+        TTM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        TTM_CUDA_TRY(cudaEventCreate(&e0));
+        TTM_CUDA_TRY(cudaEventCreate(&e1));
+        double t_reg = 0, t_smem = 0;
+        try {
+            t_reg = time_pass_df(buf.as<dcx>(), lines, base, st, e0, e1);
+            LenPlan sm = base;
+            sm.no_reg = 1;
+            t_smem = time_pass_df(buf.as<dcx>(), lines, sm, st, e0, e1);
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaStreamDestroy(st);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(st);
+        rec.reg = t_reg <= t_smem ? 1 : 0;
+        rec.us_line = std::min(t_reg, t_smem);
+    }
+    ctx->tune.push_back(rec);
+    return ctx->tune.back();
 }
 
 const TuneRec& tune_length(ttm_ctx* ctx, int L)
@@ -170,12 +242,10 @@ std::vector<int> length_candidates(int n)
 LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind)
 {
     LenPlan pl = make_len_plan(ctx->twiddles, L, kind);
-    // Double-float passes use the shared-memory Stockham kernels: the
-    // register four-step holds E complex double-float values per thread
-    // (168 registers and 78 KB of shared memory per CTA at L = 512, so 8
-    // warps per SM) and was measured slower (local sums of a 512x512x200
-    // tomogram 9.97 ms against 7.97 ms).
-    if (kind == TW_DF64) pl.no_reg = 1;
+    if (kind == TW_DF64) {
+        pl.no_reg = tune_length_df(ctx, L).reg ? 0 : 1;
+        return pl;
+    }
     if (kind != TW_F32) return pl;
     const TuneRec* r = find_rec(ctx, L);
     if (!r) return pl;
@@ -238,7 +308,7 @@ extern "C" ttm_status ttm_autotune_save(const ttm_ctx* ctx, const char* path)
     std::fprintf(f, "[\n");
     for (size_t i = 0; i < ctx->tune.size(); i++) {
         const TuneRec& r = ctx->tune[i];
-        std::fprintf(f, "  {\"L\": %d, \"reg\": %d, \"W\": %d, \"rad\": [", r.L, r.reg, r.W);
+        std::fprintf(f, "  {\"L\": %d, \"kind\": %d, \"reg\": %d, \"W\": %d, \"rad\": [", r.L, r.kind, r.reg, r.W);
         for (int s = 0; s < r.nst; s++) std::fprintf(f, "%s%d", s ? ", " : "", r.rad[s]);
         std::fprintf(f, "], \"us_line\": %.6g}%s\n", r.us_line, i + 1 < ctx->tune.size() ? "," : "");
     }
@@ -262,7 +332,8 @@ extern "C" ttm_status ttm_autotune_load(ttm_ctx* ctx, const char* path)
         TuneRec r;
         const char* q = std::strstr(line, "\"rad\": [");
         const char* u = std::strstr(line, "\"us_line\":");
-        if (!q || !u || std::sscanf(p, "\"L\": %d, \"reg\": %d, \"W\": %d", &r.L, &r.reg, &r.W) != 3 ||
+        if (!q || !u || std::sscanf(p, "\"L\": %d, \"kind\": %d, \"reg\": %d, \"W\": %d", &r.L, &r.kind, &r.reg,
+                                    &r.W) != 4 ||
             std::sscanf(u, "\"us_line\": %lf", &r.us_line) != 1) {
             ok = false;
             break;
@@ -281,7 +352,8 @@ extern "C" ttm_status ttm_autotune_load(ttm_ctx* ctx, const char* path)
         for (int s = 0; s < r.nst; s++)
             radix_ok &= (r.rad[s] == 2 || r.rad[s] == 3 || r.rad[s] == 4 || r.rad[s] == 5 || r.rad[s] == 7 ||
                          r.rad[s] == 8);
-        if (r.L < 2 || prod != r.L || !radix_ok || (r.reg != 0 && r.reg != 1) || r.W < 0 || r.W > 16) {
+        if (r.L < 2 || prod != r.L || !radix_ok || (r.reg != 0 && r.reg != 1) || r.W < 0 || r.W > 16 ||
+            (r.kind != TW_F32 && r.kind != TW_DF64)) {
             ok = false;
             break;
         }
@@ -292,7 +364,7 @@ extern "C" ttm_status ttm_autotune_load(ttm_ctx* ctx, const char* path)
     for (const auto& r : recs) {
         bool replaced = false;
         for (auto& e : ctx->tune)
-            if (e.L == r.L) { e = r; replaced = true; }
+            if (e.L == r.L && e.kind == r.kind) { e = r; replaced = true; }
         if (!replaced) ctx->tune.push_back(r);
     }
     return TTM_OK;

@@ -76,8 +76,9 @@ void peakmap_box_run(ttm_ctx* ctx, int n, const float* C, int Z, int Yin, int Xi
 void autotune_shape(ttm_ctx* ctx, const int t[3], int out[3]);
 
 // LenPlan of length L and twiddle kind: the autotuned schedule and tile
-// width when the context has one for FP32 L, else the default schedule
-// (double-float lengths: always the shared-memory passes)
+// width when the context has one for FP32 L, else the default schedule;
+// for double-float L the register / shared-memory choice is timed on first
+// use and kept in the context
 LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind);
 
 // host mask on the template grid (Sec. 2 after Eq. 3); returns M
@@ -90,6 +91,7 @@ namespace ttm {
 // and the shared-memory passes over radix schedules and tile widths
 struct TuneRec {
     int L = 0;
+    int kind = 0; // TW_F32 or TW_DF64 passes
     int reg = 0;  // 1: register kernel
     int W = 0;    // tile width of the shared-memory passes
     int nst = 0;
