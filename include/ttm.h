@@ -67,8 +67,11 @@ typedef struct ttm_mlp ttm_mlp;
  *   order_n          tensor degree n (even; 2, 4 or 6 are built)
  *   dprime           3: the weight of rotation R is (R e_z)^{(x)n}, maximised
  *                    over unit directions u in S^2 (K = binom(n+2,2));
- *                    4: quaternion powers q^{(x)n} as in Sec. 3 (oracle only
- *                    in this version: TTM_E_UNSUPPORTED on the GPU)
+ *                    4: the quaternion powers q^{(x)n} of Sec. 3, maximised
+ *                    over unit quaternions (K = binom(n+3,3): 10, 35, 84):
+ *                    a full rotation, roll included. Field and correlation
+ *                    are built for n = 2, 4, 6, the maximiser for n = 2, 4;
+ *                    the learned maximiser and the batch are d' = 3 only
  *   mask_radius      r of the spherical mask m (Sec. 2, after Eq. 3), voxels
  *   mask_soft_width  width of the raised-cosine edge beyond r; 0 = binary
  *   filter_a         a of the filter h with z-transform 1 + a(z + 1/z - 2)
@@ -114,7 +117,9 @@ ttm_status ttm_rotation_set(int64_t n_base, int cube, double* h_quats);
 /* Tensor template (Eq. 9, Alg. 1): normalises the template (Eq. 4: filter
  * h, mask m, zero mean and unit norm under the mask) into t', then
  * T_alpha(p) = (1/|Q|) sum_q u_q^alpha t'(R_q^T p) over the quadrature of
- * `params` (u_q = R_q e_z), all in FP64 on the GPU.
+ * `params` (u_q = R_q e_z for d' = 3, u_q = q for d' = 4), all in FP64 on
+ * the GPU. Components are in graded-lex descending order of the exponents
+ * of (x, y, z), or of (w, x, y, z) for d' = 4.
  *   d_tmpl   float32 [tz][ty][tx] raw template (device)
  *   d_field  float64 [K][tz][ty][tx] output (device), K = ttm_num_components
  * Blocking: returns once the field has been written. */
@@ -187,20 +192,26 @@ ttm_status ttm_plan_copy_w(ttm_plan* plan, float* d_w, void* stream);
 /* ---------------------------------------------------- steps a3-a4: Sec. 3.1-3.2 */
 
 /* Per voxel: score s(x) = max over unit u of C(x) . u^{(x)n} (the dominant
- * Z-eigenvalue, Sec. 3.1), orientation u*(x) (the maximiser, on the
- * half-sphere whose last non-zero coordinate is positive) and the Frobenius
- * proxy ||C(x)||_F (Sec. 3.2).
+ * Z-eigenvalue, Sec. 3.1), orientation u*(x) (the maximiser) and the
+ * Frobenius proxy ||C(x)||_F (Sec. 3.2).
  *   d_C       float32 [K][Z][Y][X] (device, from ttm_correlate)
- *   d_score   float32 [Z][Y][X]; d_orient float32 [3][Z][Y][X] (u_x, u_y, u_z)
+ *   d_score   float32 [Z][Y][X]
+ *   d_orient  float32 [d'][Z][Y][X]: d' = 3, the unit direction (u_x, u_y,
+ *             u_z) with its last non-zero coordinate positive; d' = 4, the
+ *             unit quaternion (w, x, y, z) with its first non-zero entry
+ *             positive (q and -q are the same rotation)
  *   d_frob    float32 [Z][Y][X] or NULL
- *   mode      TTM_MAX_PLAIN: probe directions, multi-start Newton;
- *             TTM_MAX_MLP_WARM: the MLP's direction (BF16 tensor cores) is
- *             polished by Newton and kept where the polish converged and
- *             its value is not below the best of 32 fixed probe directions;
- *             the other voxels go through the plain maximiser (their count
- *             is read with ttm_plan_fallback_count). The paper maximises
- *             with SS-HOPM (Sec. 3.1); the learned start has no counterpart
- *             there.
+ *   mode      TTM_MAX_PLAIN: probe directions (tensor-core probe product),
+ *             angularly separated starts, Newton polish;
+ *             TTM_MAX_MLP_WARM (d' = 3): the MLP's direction (BF16 tensor
+ *             cores) is polished by Newton and kept where the polish
+ *             converged, its value is not below the best of the 128 probe
+ *             directions (up to their FP16 error bound), the plain
+ *             maximiser would take one start only and the direction lies
+ *             within 20 degrees of the best probe; the other voxels go
+ *             through the plain maximiser (their count is read with
+ *             ttm_plan_fallback_count). The paper maximises with SS-HOPM
+ *             (Sec. 3.1); the learned start has no counterpart there.
  *   mlp       NULL for TTM_MAX_PLAIN; for TTM_MAX_MLP_WARM an MLP with
  *             K inputs on the plan's device. The first call after the MLP's
  *             parameters change rebuilds its BF16 image (synchronous).

@@ -388,7 +388,6 @@ extern "C" ttm_status ttm_plan_create_padded(ttm_ctx* ctx, const double* d_field
         std::string why;
         TTM_REQUIRE(out && d_field, E_INVALID_ARG, "null pointer argument");
         TTM_REQUIRE(params_ok(params, why), E_INVALID_ARG, why);
-        TTM_REQUIRE(params->dprime == 3, E_UNSUPPORTED, "the GPU path is built for d' = 3");
         TTM_REQUIRE(precision == TTM_PREC_FP32 || precision == TTM_PREC_FP16_SPECTRA ||
                         precision == TTM_PREC_BF16_SPECTRA,
                     E_INVALID_ARG, "unknown precision");

@@ -2,7 +2,8 @@
 // and the template normalisation of Eq. 4 that precedes it.
 //
 //   t' = m (S(t) - mu) / sqrt(<S(t)^2,1> - <S(t),1>^2 / M),  S(t) = m (h * t)
-//   T_alpha(p) = (1/|Q|) sum_q u_q^alpha t'(R_q^T p),  u_q = R_q e_z
+//   T_alpha(p) = (1/|Q|) sum_q u_q^alpha t'(R_q^T p),
+//   u_q = R_q e_z (d' = 3) or u_q = q itself (d' = 4, the quaternion form)
 //
 // The field kernel gives every thread one template voxel p and streams the
 // rotations through shared memory in chunks (rotation matrix and the K
@@ -86,7 +87,9 @@ __device__ __forceinline__ double trilinear64(const double* __restrict__ v, int 
 constexpr int kFieldThreads = 128;
 constexpr int kFieldChunk = 32;
 
-// qdata: per rotation 9 entries of R (row-major) then K weights u^alpha
+// qdata: per rotation 9 entries of R (row-major) then the weights u^alpha
+// of the K components [k0, k0 + K) of this launch (the host splits a large
+// component count into several launches); T points at component k0.
 template <int K>
 __global__ void __launch_bounds__(kFieldThreads)
 k_field(const double* __restrict__ tp, int tz, int ty, int tx, const double* __restrict__ qdata, int64_t nq,
@@ -230,6 +233,17 @@ void exponents3(int n, std::vector<int>& e)
         for (int b = n - a; b >= 0; b--) { e.push_back(a); e.push_back(b); e.push_back(n - a - b); }
 }
 
+// the same order for (w, x, y, z): exponents (a, b, c, d), a+b+c+d = n
+void exponents4(int n, std::vector<int>& e)
+{
+    e.clear();
+    for (int a = n; a >= 0; a--)
+        for (int b = n - a; b >= 0; b--)
+            for (int c = n - a - b; c >= 0; c--) {
+                e.push_back(a); e.push_back(b); e.push_back(c); e.push_back(n - a - b - c);
+            }
+}
+
 // device t' (FP64) of a raw float template under params; returns in tp
 void normalise_template_dev(ttm_ctx* ctx, const float* d_tmpl, int tz, int ty, int tx,
                             const ttm_field_params& fp, DevBuf& tp, cudaStream_t st)
@@ -273,7 +287,7 @@ extern "C" ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, 
         TTM_REQUIRE(tz > 0 && ty > 0 && tx > 0, E_SHAPE, "bad template shape");
         TTM_REQUIRE(params->order_n == 2 || params->order_n == 4 || params->order_n == 6, E_UNSUPPORTED,
                     "order_n must be 2, 4 or 6");
-        TTM_REQUIRE(params->dprime == 3, E_UNSUPPORTED, "the GPU field is built for d' = 3");
+        TTM_REQUIRE(params->dprime == 3 || params->dprime == 4, E_INVALID_ARG, "dprime must be 3 or 4");
         TTM_REQUIRE(params->n_rot_base > 0, E_INVALID_ARG, "n_rot_base must be positive");
         TTM_REQUIRE(params->mask_radius > 0 && params->filter_a >= 0 && params->filter_a < 0.25, E_INVALID_ARG,
                     "bad mask radius or filter parameter");
@@ -283,39 +297,55 @@ extern "C" ttm_status ttm_build_tensor_field(ttm_ctx* ctx, const float* d_tmpl, 
         normalise_template_dev(ctx, d_tmpl, tz, ty, tx, *params, tp, st);
 
         const int n = params->order_n;
+        const int dp = params->dprime;
         std::vector<double> quats;
         rotation_set(params->n_rot_base, params->cube_symmetrize != 0, quats);
         const int64_t nq = (int64_t)quats.size() / 4;
         std::vector<int> e;
-        exponents3(n, e);
-        const int K = (int)e.size() / 3;
-        const int QS = 9 + K;
-        std::vector<double> qd((size_t)nq * QS);
-        for (int64_t i = 0; i < nq; i++) {
-            double* R = &qd[(size_t)i * QS];
-            rot_of(&quats[4 * i], R);
-            const double u[3] = {R[2], R[5], R[8]};  // R e_z
-            for (int k = 0; k < K; k++) {
-                double wgt = 1.0;
-                for (int d = 0; d < 3; d++)
-                    for (int p = 0; p < e[3 * k + d]; p++) wgt *= u[d];
-                R[9 + k] = wgt;
-            }
-        }
-        DevBuf dq;
-        dq.alloc(qd.size() * sizeof(double));
-        TTM_CUDA_TRY(cudaMemcpyAsync(dq.p, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (dp == 3) exponents3(n, e); else exponents4(n, e);
+        const int K = (int)e.size() / dp;
+        // components per launch: all of them up to 35, else chunks of 28
+        // (the per-thread FP64 accumulators stay in registers)
+        const int KC = K <= 35 ? K : 28;
+        TTM_REQUIRE(K % KC == 0, E_UNSUPPORTED, "unsupported component count");
+        const int QS = 9 + KC;
         const double rmax = params->mask_radius + params->mask_soft_width + std::sqrt(3.0) + 1e-9;
         const int nvox = tz * ty * tx;
         const int grid = (int)ceil_div(nvox, kFieldThreads);
         const double inv = 1.0 / (double)nq;
-        switch (K) {
-            case 6: k_field<6><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, d_field); break;
-            case 15: k_field<15><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, d_field); break;
-            case 28: k_field<28><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, d_field); break;
-            default: throw Error{E_UNSUPPORTED, "unsupported component count"};
+        std::vector<double> qd((size_t)nq * QS);
+        DevBuf dq;
+        dq.alloc(qd.size() * sizeof(double));
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            for (int64_t i = 0; i < nq; i++) {
+                double* R = &qd[(size_t)i * QS];
+                const double* q = &quats[4 * i];
+                rot_of(q, R);
+                double u[4];
+                if (dp == 3) { u[0] = R[2]; u[1] = R[5]; u[2] = R[8]; }  // R e_z
+                else { u[0] = q[0]; u[1] = q[1]; u[2] = q[2]; u[3] = q[3]; }
+                for (int k = 0; k < KC; k++) {
+                    double wgt = 1.0;
+                    for (int d = 0; d < dp; d++)
+                        for (int p = 0; p < e[dp * (k0 + k) + d]; p++) wgt *= u[d];
+                    R[9 + k] = wgt;
+                }
+            }
+            // the previous launch reads dq: copy in stream order
+            TTM_CUDA_TRY(cudaMemcpyAsync(dq.p, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            double* Tk = d_field + (size_t)k0 * nvox;
+            switch (KC) {
+                case 6: k_field<6><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, Tk); break;
+                case 10: k_field<10><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, Tk); break;
+                case 15: k_field<15><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, Tk); break;
+                case 28: k_field<28><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, Tk); break;
+                case 35: k_field<35><<<grid, kFieldThreads, 0, st>>>(tp.as<double>(), tz, ty, tx, dq.as<double>(), nq, rmax * rmax, inv, Tk); break;
+                default: throw Error{E_UNSUPPORTED, "unsupported component count"};
+            }
+            TTM_LAUNCH_CHECK();
+            // qd is rewritten for the next chunk: the copy above must be done
+            if (k0 + KC < K) TTM_CUDA_TRY(cudaStreamSynchronize(st));
         }
-        TTM_LAUNCH_CHECK();
         // tp and dq are freed on return: wait for the kernel that reads them
         TTM_CUDA_TRY(cudaStreamSynchronize(st));
         return TTM_OK;

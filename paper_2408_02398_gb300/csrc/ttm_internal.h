@@ -84,6 +84,17 @@ LenPlan ctx_len_plan(ttm_ctx* ctx, int L, int kind);
 // host mask on the template grid (Sec. 2 after Eq. 3); returns M
 double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<double>& m);
 
+// the rotation quadrature of Eq. 9 (n_base super-Fibonacci quaternions,
+// optionally times the 24 cube rotations) and the graded-lex descending
+// exponents of (w, x, y, z) with sum n (4 per component)
+void rotation_set(int64_t n_base, bool cube, std::vector<double>& q);
+void exponents4(int n, std::vector<int>& e);
+// probe tables of the quaternion maximiser, and the maximiser itself over
+// all V voxels (orient: [4][V] unit quaternions)
+void upload_probe_tables4(ttm_ctx* ctx);
+void peakmap4_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
+                  cudaStream_t st);
+
 }  // namespace ttm
 
 namespace ttm {
@@ -110,6 +121,8 @@ struct ttm_ctx {
     size_t probe_off[5] = {0, 0, 0, 0, 0};
     ttm::DevBuf probe_half;    // FP16 monomial tables for the tensor-core probe product
     size_t probe_half_off[3] = {0, 0, 0};
+    ttm::DevBuf probe4;        // quaternion maximiser: probe quaternions and FP16 monomials
+    size_t probe4_off[3] = {0, 0, 0};
 };
 
 struct ttm_plan {

@@ -970,12 +970,19 @@ extern "C" ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximis
         TTM_REQUIRE(mode == TTM_MAX_MLP_WARM || mlp == nullptr, E_INVALID_ARG,
                     "mlp must be NULL for the plain maximiser");
         TTM_REQUIRE(mode == TTM_MAX_PLAIN || mlp != nullptr, E_INVALID_ARG, "the learned maximiser needs an mlp");
-        TTM_REQUIRE(plan->fp.dprime == 3, E_UNSUPPORTED, "the GPU maximiser works on the 2-sphere (d' = 3)");
+        TTM_REQUIRE(plan->fp.dprime == 3 || mode == TTM_MAX_PLAIN, E_UNSUPPORTED,
+                    "the learned maximiser works on the 2-sphere (d' = 3)");
+        TTM_REQUIRE(plan->fp.dprime == 3 || plan->fp.order_n <= 4, E_UNSUPPORTED,
+                    "the quaternion maximiser is built for n = 2 and 4");
         TTM_CUDA_TRY(cudaSetDevice(plan->ctx->device));
         const Prep& p = plan->prep;
         const int64_t V = (int64_t)p.Z * p.Y * p.X;
         cudaStream_t st = (cudaStream_t)stream;
-        if (mode == TTM_MAX_MLP_WARM) {
+        if (plan->fp.dprime == 4) {
+            stage_begin(plan, st);
+            peakmap4_run(plan->ctx, plan->fp.order_n, d_C, V, d_score, d_orient, d_frob, st);
+            stage_end(plan, ST_PEAKMAP, st);
+        } else if (mode == TTM_MAX_MLP_WARM) {
             ttm_mlp* M = const_cast<ttm_mlp*>(mlp);
             TTM_REQUIRE(M->K == plan->K, E_INVALID_ARG, "mlp input count differs from the plan's component count");
             TTM_REQUIRE(M->ctx->device == plan->ctx->device, E_INVALID_ARG, "mlp lives on another device");

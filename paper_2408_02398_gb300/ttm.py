@@ -220,6 +220,9 @@ class Plan:
                  work_shape=None):
         import torch
         K, tz, ty, tx = d_field.shape
+        if K != ttm_num_components(p.order_n, p.dprime):
+            raise ValueError("the field has %d components; order %d, d' = %d needs %d"
+                             % (K, p.order_n, p.dprime, ttm_num_components(p.order_n, p.dprime)))
         Z, Y, X = shape
         Zw, Yw, Xw = shape if work_shape is None else work_shape
         h = _vp()
@@ -264,9 +267,16 @@ def ttm_plan_copy_w(plan: Plan, d_w, stream=None):
 
 
 def ttm_peak_map(plan: Plan, d_C, d_score, d_orient, d_frob=None, mode=TTM_MAX_PLAIN, mlp=None, stream=None):
+    """Score, orientation and Frobenius maps on the plan's working grid;
+    d_orient holds d' components per voxel: (u_x, u_y, u_z) for d' = 3, the
+    unit quaternion (w, x, y, z) for d' = 4."""
     import torch
     if mlp is not None and mode == TTM_MAX_PLAIN:
         mode = TTM_MAX_MLP_WARM
+    V = int(np.prod(plan.shape))
+    if d_C.numel() < plan.K * V or d_score.numel() < V or d_orient.numel() < plan.params.dprime * V or \
+            (d_frob is not None and d_frob.numel() < V):
+        raise ValueError("map buffers are smaller than the plan's working grid needs")
     plan.ctx.check(lib().ttm_peak_map(plan.h, _dev(d_C, torch.float32, "d_C"), mode,
                                       None if mlp is None else mlp.h,
                                       _dev(d_score, torch.float32, "d_score"),
@@ -498,7 +508,7 @@ class Matcher:
         Z, Y, X = shape
         self.C = torch.empty((K, Z, Y, X), dtype=torch.float32, device=device)
         self.score = torch.empty((Z, Y, X), dtype=torch.float32, device=device)
-        self.orient = torch.empty((3, Z, Y, X), dtype=torch.float32, device=device)
+        self.orient = torch.empty((p.dprime, Z, Y, X), dtype=torch.float32, device=device)
         self.frob = torch.empty((Z, Y, X), dtype=torch.float32, device=device)
 
     def run(self, d_tomo, stream=None, mlp=None):

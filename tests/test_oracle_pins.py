@@ -406,6 +406,67 @@ def test_maximiser_order2_is_top_eigenpair():
         assert abs(abs(u[i] @ V[:, -1]) - 1) < 1e-10
 
 
+def test_quaternion_order2_is_top_eigenpair():
+    """d' = 4, n = 2: p(q) = q^T A q with A_ij = C_{e_i + e_j} (4 x 4), so
+    the maximum over unit quaternions is the top eigenpair of A; the
+    canonical quaternion has its first non-zero entry (w) positive."""
+    idx = {tuple(a): k for k, a in enumerate(O.multi_indices(2, 4))}
+    C = synth.random_tensors(18, 40, 10).T.copy()
+    s, u, _ = O.maximise(C, 2, 4, nsamples=4000)
+    for i in range(C.shape[1]):
+        A = np.empty((4, 4))
+        for a in range(4):
+            for b in range(4):
+                e = [0, 0, 0, 0]
+                e[a] += 1
+                e[b] += 1
+                A[a, b] = C[idx[tuple(e)], i]
+        ev, V = np.linalg.eigh(A)
+        assert s[i] == pytest.approx(ev[-1], abs=1e-12)
+        assert abs(abs(u[i] @ V[:, -1]) - 1) < 1e-10
+        assert u[i][0] > 0
+
+
+def test_quaternion_rank_one_and_two():
+    """d' = 4, n = 4: C = l1 q1^{(x)4} + l2 q2^{(x)4} with orthogonal unit
+    quaternions has its maximum l1 at +-q1."""
+    rng = np.random.default_rng(44)
+    a = O.multi_indices(4, 4)
+    for _ in range(5):
+        Qm, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+        q1, q2 = Qm[:, 0], Qm[:, 1]
+        c = np.array([2.0 * np.prod(q1 ** e) + 1.3 * np.prod(q2 ** e) for e in a])
+        s, u, _ = O.maximise(c[:, None], 4, 4, nsamples=8000)
+        assert s[0] == pytest.approx(2.0, abs=1e-12)
+        assert abs(abs(u[0] @ q1) - 1) < 1e-10
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_quaternion_form_recovers_planted_rotation(n):
+    """Sec. 3: with d' = 4 the maximising quaternion is the full rotation
+    (roll included) of a planted copy. The copies are placed by the input
+    generator's own resampler at rotations it draws (not by the oracle);
+    the order-n smoothing of Eq. 9 biases the maximum by a few degrees, so
+    the bound is 10 degrees."""
+    N, r, shape = 16, 7.0, (40, 40, 40)
+    tmpl = synth.gaussian_blob_template(N, seed=20240802)
+    m, _ = O.mask(tmpl.shape, r)
+    tp, _ = O.normalise_template(tmpl, m)
+    field = O.tensor_field(tp, O.rotation_set(512), n, 4)
+    for seed in range(3):
+        vol, pl = synth.make_tomogram(shape, tmpl, r, 1, seed=100 + seed, amplitude=5.0)
+        c = pl.centres[0]
+        pr = O.Prepared(vol.astype(np.float64), tmpl, r)
+        v = np.array([(c[0] * shape[1] + c[1]) * shape[2] + c[2]])
+        w, _, _ = O.local_w(pr.g, pr.m, v, periodic=False, floor=pr.floor)
+        C = O.correlate(pr.g, field, v, periodic=False, w=w)
+        s, u, _ = O.maximise(C, n, 4, nsamples=20000)
+        R0, R1 = O.quat_to_rot(pl.quats[0]), O.quat_to_rot(u[0])
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R0.T @ R1) - 1) / 2))))
+        assert ang < 10.0, (seed, ang)
+        assert s[0] > 0
+
+
 @pytest.mark.parametrize("n", [2, 4, 6])
 def test_maximiser_rank_one_and_two(n):
     rng = np.random.default_rng(n)
