@@ -159,7 +159,7 @@ __device__ __forceinline__ float lmin3(float h00, float h01, float h02, float h1
     const float pp = (a * a + b * b + c * c + 2.f * off) * (1.f / 6.f);
     if (pp <= 0.f) return m;
     const float s = sqrtf(pp);
-    const float is = 1.f / s;
+    const float is = __fdividef(1.f, s);
     const float B00 = a * is, B11 = b * is, B22 = c * is, B01 = h01 * is, B02 = h02 * is, B12 = h12 * is;
     const float det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
     const float r = fminf(1.f, fmaxf(-1.f, 0.5f * det));
@@ -173,15 +173,19 @@ __device__ __forceinline__ float lmin3(float h00, float h01, float h02, float h1
 __device__ __forceinline__ void newton_dir4(float h00, float h01, float h02, float h11, float h12, float h22,
                                             const float* g, float frob, float* x)
 {
+    // pivots d_i and their fast reciprocals r_i (the step is only a
+    // proposal: backtracking and the monotone fallback guard it)
     const float eps = 1e-6f * frob;
-    float d0 = h00, l10 = 0.f, l20 = 0.f, d1 = 0.f, l21 = 0.f, d2 = 0.f;
+    float d0 = h00, r0 = 0.f, l10 = 0.f, l20 = 0.f, d1 = 0.f, r1 = 0.f, l21 = 0.f, d2 = 0.f;
     bool pd = d0 > eps;
     if (pd) {
-        l10 = h01 / d0; l20 = h02 / d0;
+        r0 = __fdividef(1.f, d0);
+        l10 = h01 * r0; l20 = h02 * r0;
         d1 = h11 - l10 * h01;
         pd = d1 > eps;
         if (pd) {
-            l21 = (h12 - l20 * h01) / d1;
+            r1 = __fdividef(1.f, d1);
+            l21 = (h12 - l20 * h01) * r1;
             d2 = h22 - l20 * l20 * d0 - l21 * l21 * d1;
             pd = d2 > eps;
         }
@@ -190,15 +194,17 @@ __device__ __forceinline__ void newton_dir4(float h00, float h01, float h02, flo
         const float sh = 0.05f * frob - lmin3(h00, h01, h02, h11, h12, h22);
         h00 += sh; h11 += sh; h22 += sh;
         d0 = h00;
-        l10 = h01 / d0; l20 = h02 / d0;
+        r0 = __fdividef(1.f, d0);
+        l10 = h01 * r0; l20 = h02 * r0;
         d1 = h11 - l10 * h01;
-        l21 = (h12 - l20 * h01) / d1;
+        r1 = __fdividef(1.f, d1);
+        l21 = (h12 - l20 * h01) * r1;
         d2 = h22 - l20 * l20 * d0 - l21 * l21 * d1;
     }
     const float y0 = g[0], y1 = g[1] - l10 * y0, y2 = g[2] - l20 * y0 - l21 * y1;
-    x[2] = y2 / d2;
-    x[1] = y1 / d1 - l21 * x[2];
-    x[0] = y0 / d0 - l10 * x[1] - l20 * x[2];
+    x[2] = __fdividef(y2, d2);
+    x[1] = y1 * r1 - l21 * x[2];
+    x[0] = y0 * r0 - l10 * x[1] - l20 * x[2];
     const float xn2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     if (xn2 > 0.25f) {
         const float sc = 0.5f * rsqrtf(xn2);
@@ -315,7 +321,7 @@ __device__ __forceinline__ int key_at(int c, int col) { return 2 * ((c >> 1) * k
 template <int N>
 __host__ __device__ constexpr size_t p4_smem_bytes()
 {
-    return p4_key_bytes(N) + sizeof(float4) * kP4 + sizeof(__half) * (size_t)kP4 * p4_kxs(N);
+    return p4_key_bytes(N) + sizeof(float4) * kP4 + sizeof(__half) * (size_t)kP4 * p4_kxs(N) + sizeof(uint2) * kP4;
 }
 
 template <int N>
@@ -333,11 +339,18 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
     uint32_t* xs = reinterpret_cast<uint32_t*>(p4_smem);  // staged input (aliases the keys)
     float4* sdir = reinterpret_cast<float4*>(p4_smem + p4_key_bytes(N));
     __half* phih = reinterpret_cast<__half*>(sdir + kP4);
+    // FP16 copies of the directions, only for the 25-degree separation tests
+    uint2* sdirh = reinterpret_cast<uint2*>(phih + kP4 * KXS);
     {
         const uint4* src = reinterpret_cast<const uint4*>(N == 2 ? tabs.phi2h : tabs.phi4h);
         uint4* dst = reinterpret_cast<uint4*>(phih);
         for (int i = threadIdx.x; i < kP4 * KXS / 8; i += blockDim.x) dst[i] = src[i];
-        for (int i = threadIdx.x; i < kP4; i += blockDim.x) sdir[i] = tabs.dir[i];
+        for (int i = threadIdx.x; i < kP4; i += blockDim.x) {
+            const float4 d = tabs.dir[i];
+            sdir[i] = d;
+            const __half2 a = __floats2half2_rn(d.x, d.y), b = __floats2half2_rn(d.z, d.w);
+            sdirh[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -432,9 +445,11 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             __syncwarp();
         }
         // starts: the best probe, then by angular suppression over the cell
-        // bests (each pass drops the cells whose best lies within 25 degrees
-        // of the newest start, or more than 0.2 ||C||_F below the best, and
-        // takes the best remaining one). Start rows are packed 9 bits each.
+        // bests: the first pass keeps the cells within 0.2 ||C||_F of the
+        // best (an integer compare of keys) that lie farther than 25 degrees
+        // from it; each later start is the best kept cell, and the next pass
+        // (over the kept cells only) drops those within 25 degrees of it.
+        // Start rows are packed 9 bits each.
         uint64_t rows = 0;
         int ns = 1;
         {
@@ -447,26 +462,46 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             }
             int last = p4_row(bc, best & 7u);
             rows = (uint64_t)last;
-            const float thrv = hkey_value(best) - kP4Margin;
-            uint64_t alive = ~0ull;
-#pragma unroll 1
-            for (int s = 1; s < kStarts; s++) {
+            const uint32_t thr = hkey(hkey_value(best) - kP4Margin, 0u);
+            uint64_t alive = 0ull;
+            uint32_t bk = 0u;
+            int bcell = -1;
+            {
                 const float4 ds = sdir[last];
-                uint32_t bk = 0u;
-                int bcell = -1;
 #pragma unroll 4
                 for (int cl = 0; cl < kP4Cells; cl++) {
-                    if (!((alive >> cl) & 1ull)) continue;
                     const uint32_t kk = keys[key_at(cl, threadIdx.x)];
-                    const float4 dj = sdir[p4_row(cl, kk & 7u)];
-                    const float dt = fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z + dj.w * ds.w);
-                    if (dt >= kP4SepCos || hkey_value(kk) < thrv) alive &= ~(1ull << cl);
-                    else if (kk > bk) { bk = kk; bcell = cl; }
+                    if (kk < thr) continue;
+                    const uint2 dh = sdirh[p4_row(cl, kk & 7u)];
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&dh.x));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&dh.y));
+                    const float dt = fabsf(a.x * ds.x + a.y * ds.y + b.x * ds.z + b.y * ds.w);
+                    if (dt < kP4SepCos) {
+                        alive |= 1ull << cl;
+                        if (kk > bk) { bk = kk; bcell = cl; }
+                    }
                 }
-                if (bcell < 0) break;
+            }
+#pragma unroll 1
+            for (int s = 1; s < kStarts && bcell >= 0; s++) {
                 last = p4_row(bcell, bk & 7u);
                 rows |= (uint64_t)last << (9 * s);
                 ns = s + 1;
+                alive &= ~(1ull << bcell);
+                if (s + 1 == kStarts) break;
+                const float4 ds = sdir[last];
+                bk = 0u;
+                bcell = -1;
+                for (uint64_t m = alive; m; m &= m - 1) {
+                    const int cl = __ffsll((long long)m) - 1;
+                    const uint32_t kk = keys[key_at(cl, threadIdx.x)];
+                    const uint2 dh = sdirh[p4_row(cl, kk & 7u)];
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&dh.x));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&dh.y));
+                    const float dt = fabsf(a.x * ds.x + a.y * ds.y + b.x * ds.z + b.y * ds.w);
+                    if (dt >= kP4SepCos) alive &= ~(1ull << cl);
+                    else if (kk > bk) { bk = kk; bcell = cl; }
+                }
             }
         }
         __syncwarp();  // the key rows are restaged by the next voxel block
