@@ -461,10 +461,21 @@ def run_quaternion(args):
         C = torch.empty((K, Z, Y, X), device=dev)
         score = torch.empty((Z, Y, X), device=dev)
         orient = torch.empty((dp, Z, Y, X), device=dev)
+        frob = torch.empty((Z, Y, X), device=dev)
         ms_corr = _timed(lambda: ttm.ttm_correlate(plan, d_tomo, C), args.steps, args.warmup, stream)
-        ms_pm = _timed(lambda: ttm.ttm_peak_map(plan, C, score, orient), args.steps, args.warmup, stream)
+        ms_pm = _timed(lambda: ttm.ttm_peak_map(plan, C, score, orient, frob), args.steps, args.warmup, stream)
         res[dp] = {"components": K, "correlate_ms": ms_corr, "peak_map_ms": ms_pm,
                    "voxels_per_s": V / ((ms_corr + ms_pm) / 1e3)}
+        if dp == 4:
+            # TTM-ref (Alg. 3) on the P = 300 highest peaks of the Frobenius map (Sec. 3.2)
+            pk, _ = ttm.ttm_find_peaks(plan, frob, 300, 2.0 * r)
+            ttm.ttm_refine_peaks(plan, t, orient, pk, 3.0)
+            t_ref = time.perf_counter()
+            ridx, _, _ = ttm.ttm_refine_peaks(plan, t, orient, pk, 3.0)
+            res[dp]["refine"] = {"peaks": int(pk.size), "r_s": 3.0, "candidates_per_peak": 123,
+                                 "ms": (time.perf_counter() - t_ref) * 1e3,
+                                 "moved_frac": float(np.mean(ridx != pk)),
+                                 "note": "host-timed call (H2D of the list, kernel, D2H, host selection)"}
         cen = np.array([(int(c[0]) * Y + int(c[1])) * X + int(c[2]) for c in wl.planted.centres])
         oc = orient.reshape(dp, -1)[:, torch.as_tensor(cen, device=dev)].cpu().numpy().T
         if dp == 3:
@@ -474,7 +485,7 @@ def run_quaternion(args):
             got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
             sg = score.flatten()[tv].cpu().numpy()
             qc = oc
-        del plan, C, score, orient, field
+        del plan, C, score, orient, field, frob
     ck = clocks.stop()
     pr = O.Prepared(wl.tomo, wl.template, r)
     ofield = O.tensor_field(pr.tp, O.rotation_set(64), n, 4)

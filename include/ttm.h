@@ -308,6 +308,27 @@ ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, int Z, int Y
                                   const int* box, int P, double min_dist, int64_t* h_idx,
                                   float* h_val, int* h_count, void* stream);
 
+/* Position refinement, TTM-ref (Sec. 3.3, Alg. 3). For each peak x_i the
+ * voxels x of the ball ||x - x_i|| <= r_s (x_i first, then the rest in
+ * z, y, x order) inside the valid box are scored by the LNCC at their own
+ * optimal rotation, c(x) = w(x) sum_z t'(R(q*(x))^T z) g(x + z), evaluated
+ * in real space over the template window (trilinear samples of t', FP32
+ * samples, FP64 reduction); the first strictly highest voxel in that order
+ * is kept (the paper uses r_s = 3).
+ *   plan      a d' = 4 plan after ttm_correlate: g and w of that call are used
+ *   d_tmpl    float32 [tz][ty][tx] raw template (device); normalised here by
+ *             Eq. 4 with the plan's parameters, as in ttm_build_tensor_field
+ *   d_orient  float32 [4][Z][Y][X] quaternion map of ttm_peak_map (device)
+ *   h_peaks   int64 [P] linear voxel indices on the plan's working grid,
+ *             each inside the valid box (host); P <= 65535
+ *   h_idx     int64 [P] refined voxel indices; h_quat float32 [P][4] its
+ *             rotation (w, x, y, z); h_lncc float32 [P] its LNCC (host)
+ * Allocates a small per-call workspace; synchronises `stream`. Errors:
+ * TTM_E_UNSUPPORTED for a d' = 3 plan, TTM_E_INVALID_ARG for a peak outside
+ * the valid box or r_s outside [0, 16]. */
+ttm_status ttm_refine_peaks(ttm_plan* plan, const float* d_tmpl, const float* d_orient, const int64_t* h_peaks,
+                            int P, double r_s, int64_t* h_idx, float* h_quat, float* h_lncc, void* stream);
+
 /* ------------------------------------------------------- step a6: Eqs. 1, 6, 7 */
 
 /* Classical template matching baseline: for every rotation q_j of h_quats

@@ -14,6 +14,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import math
+
 import numpy as np
 
 from . import build as _build
@@ -340,6 +342,57 @@ def tm(g, tp, quats, vox=None, periodic: bool = False, w=None):
     lib().oracle_tm(_p(g), Z, Y, X, _p(tp), tz, ty, tx, _p(quats), quats.shape[0],
                     int(periodic), _p(v, _pi64), v.size, _p(wv), _p(best), _p(bidx, _pi32))
     return best, bidx
+
+
+def ball_offsets(r_s: float) -> np.ndarray:
+    """Alg. 3's candidates around a peak in the order they are visited: the
+    peak itself, then every other offset d with |d| <= r_s in (z, y, x)
+    lexicographic order; rows (dz, dy, dx)."""
+    R = int(math.floor(r_s))
+    out = [(0, 0, 0)]
+    for dz in range(-R, R + 1):
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                if (dz, dy, dx) != (0, 0, 0) and dz * dz + dy * dy + dx * dx <= r_s * r_s:
+                    out.append((dz, dy, dx))
+    return np.array(out, dtype=np.int64)
+
+
+def ttm_refine(pr, field, n: int, peaks, r_s: float = 3.0, nsamples: int = 20000):
+    """TTM-ref (Sec. 3.3, Alg. 3) with d' = 4: for each peak, every ball
+    voxel inside the valid interior gets its optimal rotation from its own C
+    (Eq. 8, then the maximiser over unit quaternions) and the LNCC at that
+    single rotation (Eq. 1 / Eq. 7 via tm); the first strictly highest
+    voxel in the order of ball_offsets is kept. pr is a Prepared set, field
+    the d' = 4 tensor field. Returns (indices, quaternions [P][4], LNCC [P],
+    per-peak lists of (candidate indices, their LNCC))."""
+    Z, Y, X = pr.g.shape
+    tz, ty, tx = pr.tshape
+    lo = np.array([tz // 2, ty // 2, tx // 2])
+    hi = np.array([Z - (tz - tz // 2), Y - (ty - ty // 2), X - (tx - tx // 2)])
+    offs = ball_offsets(r_s)
+    idx, quats, vals, cands = [], [], [], []
+    for pk in np.asarray(peaks, dtype=np.int64):
+        c0 = np.array([pk // (Y * X), (pk // X) % Y, pk % X])
+        pos = c0[None, :] + offs
+        ok = np.all((pos >= lo) & (pos <= hi), axis=1)
+        if not ok[0]:
+            raise ValueError("peak outside the valid interior")
+        pos = pos[ok]
+        vox = (pos[:, 0] * Y + pos[:, 1]) * X + pos[:, 2]
+        w, _, _ = local_w(pr.g, pr.m, vox, False, pr.floor)
+        C = correlate(pr.g, field, vox, False, w)
+        _, q, _ = maximise(C, n, 4, nsamples)
+        c = np.array([tm(pr.g, pr.tp, q[k], vox[k:k + 1], False, w[k:k + 1])[0][0] for k in range(vox.size)])
+        best = 0
+        for k in range(1, vox.size):
+            if c[k] > c[best]:
+                best = k
+        idx.append(int(vox[best]))
+        quats.append(q[best])
+        vals.append(float(c[best]))
+        cands.append((vox, c))
+    return np.array(idx, dtype=np.int64), np.array(quats).reshape(-1, 4), np.array(vals), cands
 
 
 # ------------------------------------------------------- learned start ---

@@ -88,6 +88,10 @@ double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<doub
 // optionally times the 24 cube rotations) and the graded-lex descending
 // exponents of (w, x, y, z) with sum n (4 per component)
 void rotation_set(int64_t n_base, bool cube, std::vector<double>& q);
+// t' of Eq. 4 (filter, mask, zero mean and unit norm under the mask) of a
+// raw float template, FP64 on the device, returned in tp
+void normalise_template_dev(ttm_ctx* ctx, const float* d_tmpl, int tz, int ty, int tx, const ttm_field_params& fp,
+                            DevBuf& tp, cudaStream_t st);
 void exponents4(int n, std::vector<int>& e);
 // probe tables of the quaternion maximiser, and the maximiser itself over
 // all V voxels (orient: [4][V] unit quaternions)

@@ -35,7 +35,7 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_
            "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
            "ttm_mlp_load", "ttm_plan_create_padded", "ttm_autotune_shape", "ttm_autotune_entries",
            "ttm_autotune_save", "ttm_autotune_load", "ttm_batch_create", "ttm_batch_run", "ttm_batch_work_shape",
-           "ttm_batch_destroy"]
+           "ttm_batch_destroy", "ttm_refine_peaks"]
 
 
 class TTMError(RuntimeError):
@@ -91,6 +91,7 @@ def lib():
             "ttm_plan_set_localsum": (_i, [_vp, _i]),
             "ttm_find_peaks_noalloc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _d, _vp, _vp, C.POINTER(_i), _vp]),
             "ttm_plan_fallback_count": (_i, [_vp, C.POINTER(_i64), _vp]),
+            "ttm_refine_peaks": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp]),
             "ttm_mlp_num_params": (_i64, [_i]),
             "ttm_mlp_create": (_i, [_vp, _i, C.c_uint64, C.POINTER(_vp)]),
             "ttm_mlp_destroy": (None, [_vp]),
@@ -447,6 +448,24 @@ def ttm_find_peaks(plan: Plan, d_map, P: int, min_dist: float, stream=None):
     plan.ctx.check(lib().ttm_find_peaks(plan.h, _dev(d_map, torch.float32, "d_map"), P, float(min_dist),
                                         idx.ctypes.data, val.ctypes.data, C.byref(n), _stream(stream)))
     return idx[:n.value], val[:n.value]
+
+
+def ttm_refine_peaks(plan: Plan, d_tmpl, d_orient, peaks, r_s: float = 3.0, stream=None):
+    """TTM-ref (Alg. 3): refined linear indices, rotations (w, x, y, z) and
+    LNCC values of the peaks (linear indices on the plan's working grid)."""
+    import torch
+    pk = np.ascontiguousarray(peaks, dtype=np.int64)
+    P = int(pk.size)
+    if d_orient.numel() < 4 * int(np.prod(plan.shape)):
+        raise ValueError("d_orient must hold the [4][Z][Y][X] quaternion map")
+    idx = np.zeros(max(P, 1), dtype=np.int64)
+    quat = np.zeros((max(P, 1), 4), dtype=np.float32)
+    lncc = np.zeros(max(P, 1), dtype=np.float32)
+    plan.ctx.check(lib().ttm_refine_peaks(plan.h, _dev(d_tmpl, torch.float32, "d_tmpl"),
+                                          _dev(d_orient, torch.float32, "d_orient"), pk.ctypes.data, P,
+                                          float(r_s), idx.ctypes.data, quat.ctypes.data, lncc.ctypes.data,
+                                          _stream(stream)))
+    return idx[:P], quat[:P], lncc[:P]
 
 
 def ttm_find_peaks_noalloc(ctx: Context, d_map, box, P: int, min_dist: float, stream=None):

@@ -232,3 +232,53 @@ def test_quaternion_unsupported_forms(T, ctx):
     assert e.value.code == 3
     with pytest.raises(ValueError):      # a d' = 3 sized orientation map is too small
         T.ttm_peak_map(plan, d_C, d_s, torch.empty((3, 16, 16, 16), device="cuda"))
+
+
+# ------------------------------------------------------------- TTM-ref --
+
+def test_ttm_refine_matches_oracle(T, ctx):
+    """Alg. 3 on the GPU (quaternion map, real-space LNCC per candidate)
+    against the oracle's TTM-ref (its own field, C, maximiser and LNCC) for
+    peaks at, and 1-2 voxels off, a planted copy and one in pure noise. The
+    refined voxel is unique where the oracle's best candidate leads the next
+    by more than 1e-4; elsewhere the GPU's choice must be within 1e-4 of the
+    oracle's best LNCC."""
+    N, r, n, shape = 16, 7.0, 4, (40, 40, 40)
+    tmpl = synth.gaussian_blob_template(N, seed=20240802).astype(np.float32)
+    vol, pl = synth.make_tomogram(shape, tmpl, r, 1, seed=101, amplitude=5.0)
+    p = T.params(order_n=n, mask_radius=r, n_rot_base=256, dprime=4)
+    m = T.Matcher(ctx, tmpl, p, shape)
+    m.run(dev(vol))
+    torch.cuda.synchronize()
+    c = np.array(pl.centres[0], dtype=np.int64)
+    Y, X = shape[1], shape[2]
+    lin = lambda z, y, x: (z * Y + y) * X + x
+    far = (c + np.where(c < 20, 10, -10))              # a valid voxel away from the copy
+    starts = np.array([lin(*c), lin(c[0] + 1, c[1] - 1, c[2] + 2), lin(c[0] - 2, c[1], c[2]), lin(*far)])
+    idx, q, val = T.ttm_refine_peaks(m.plan, dev(tmpl), m.orient, starts, 3.0)
+    pr = O.Prepared(vol.astype(np.float64), tmpl.astype(np.float64), r)
+    field = O.tensor_field(pr.tp, O.rotation_set(256), n, 4)
+    oidx, oq, oval, cands = O.ttm_refine(pr, field, n, starts, r_s=3.0)
+    for k in range(len(starts)):
+        vox, cv = cands[k]
+        j = np.flatnonzero(vox == idx[k])
+        assert j.size == 1
+        assert cv.max() - cv[j[0]] <= 1e-4
+        top2 = np.sort(cv)[-2:]
+        if top2[1] - top2[0] > 1e-4:
+            assert idx[k] == oidx[k]
+        assert abs(val[k] - cv[j[0]]) <= 1e-4
+        if k < 3:
+            assert idx[k] == lin(*c)
+            assert rot_angle_deg(q[k][None], oq[k][None])[0] <= ANG_TOL_DEG
+            assert rot_angle_deg(q[k][None], np.asarray(pl.quats[0])[None])[0] < 10.0
+    # an empty list, a peak outside the valid box, and a d' = 3 plan
+    assert len(T.ttm_refine_peaks(m.plan, dev(tmpl), m.orient, [], 3.0)[0]) == 0
+    with pytest.raises(T.TTMError) as e:
+        T.ttm_refine_peaks(m.plan, dev(tmpl), m.orient, [0], 3.0)
+    assert e.value.code == 1
+    p3 = T.params(order_n=2, mask_radius=r, n_rot_base=16)
+    m3 = T.Matcher(ctx, tmpl, p3, shape)
+    with pytest.raises(T.TTMError) as e:
+        T.ttm_refine_peaks(m3.plan, dev(tmpl), m.orient, starts[:1], 3.0)
+    assert e.value.code == 3

@@ -467,6 +467,38 @@ def test_quaternion_form_recovers_planted_rotation(n):
         assert s[0] > 0
 
 
+def test_ttm_refine_moves_shifted_peak_to_planted_centre():
+    """Alg. 3: a peak placed 1-2 voxels off a planted copy moves back to the
+    copy's centre (placed by the input generator, not the oracle), with the
+    copy's rotation, and the LNCC there exceeds the LNCC at the shifted
+    start. The candidate set is the ball of radius 3 (123 voxels) in
+    (z, y, x) order after the peak itself."""
+    offs = O.ball_offsets(3.0)
+    assert len(offs) == 123 and tuple(offs[0]) == (0, 0, 0)
+    assert (np.sum(offs ** 2, axis=1) <= 9).all()
+    assert [tuple(o) for o in offs[1:]] == sorted(tuple(o) for o in offs[1:])
+    N, r, n, shape = 16, 7.0, 4, (40, 40, 40)
+    tmpl = synth.gaussian_blob_template(N, seed=20240802)
+    vol, pl = synth.make_tomogram(shape, tmpl, r, 1, seed=101, amplitude=5.0)
+    pr = O.Prepared(vol.astype(np.float64), tmpl, r)
+    field = O.tensor_field(pr.tp, O.rotation_set(256), n, 4)
+    c = np.array(pl.centres[0], dtype=np.int64)
+    Y, X = shape[1], shape[2]
+    true = (c[0] * Y + c[1]) * X + c[2]
+    starts = [true, ((c[0] + 1) * Y + c[1] - 1) * X + c[2] + 2, ((c[0] - 2) * Y + c[1]) * X + c[2]]
+    idx, q, val, cands = O.ttm_refine(pr, field, n, starts, r_s=3.0, nsamples=8000)
+    assert (idx == true).all()
+    for k in range(3):
+        R0, R1 = O.quat_to_rot(pl.quats[0]), O.quat_to_rot(q[k])
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R0.T @ R1) - 1) / 2))))
+        assert ang < 10.0
+        vox, cv = cands[k]
+        assert val[k] == cv.max()
+        if k > 0:
+            assert val[k] > cv[0] + 0.05          # better than at the shifted start
+    assert val[0] > 0.9                            # the copy dominates its window (amplitude 5)
+
+
 @pytest.mark.parametrize("n", [2, 4, 6])
 def test_maximiser_rank_one_and_two(n):
     rng = np.random.default_rng(n)
