@@ -329,6 +329,47 @@ ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, int Z, int Y
 ttm_status ttm_refine_peaks(ttm_plan* plan, const float* d_tmpl, const float* d_orient, const int64_t* h_peaks,
                             int P, double r_s, int64_t* h_idx, float* h_quat, float* h_lncc, void* stream);
 
+/* ------------------------------------- block processing: Sec. 3.4 */
+
+/* The z-slab partition of block processing (host only). For a tomogram of
+ * Z planes and a template of tz planes (centre cz = tz / 2; valid planes
+ * [cz, Z - (tz - cz) + 1)), slab k gets the output planes [o0, o1) (slab_z
+ * of the valid planes, the last one ragged), its map planes [m0, m1) =
+ * [o0, o1) widened by one valid plane each side (the 26-neighbour test), and
+ * its input planes [i0, i1) = the map planes' template windows plus one
+ * plane each side for the 3-tap filter, clipped to the tomogram. Writes up
+ * to cap rows (o0, o1, m0, m1, i0, i1) to out (may be NULL) and returns the
+ * slab count, or -1 for bad arguments. */
+int ttm_slab_ranges(int Z, int tz, int slab_z, int* out, int cap);
+
+/* Merge Peaks (Sec. 3.4, host only): orders n candidates (linear indices
+ * on a Z x Y x X grid, values) by value descending then index ascending and
+ * accepts greedily those at Euclidean distance >= min_dist from every one
+ * accepted before, up to P. Returns the count written to out_idx / out_val,
+ * or -1 for bad arguments. Find Peaks is this applied to the strict
+ * 26-neighbour maxima of a map. */
+int ttm_merge_peaks(int64_t n, const int64_t* idx, const float* val, int Z, int Y, int X, int P, double min_dist,
+                    int64_t* out_idx, float* out_val);
+
+/* Block processing (Sec. 3.4): Find Peaks of the score map (map_kind 0) or
+ * of the Frobenius map (map_kind 1) of a tomogram held in HOST memory,
+ * float32 [Z][Y][X], processed in z-slabs of slab_z output planes
+ * (ttm_slab_ranges). Each slab is copied to the device, correlated on its
+ * own autotuned working grid (one plan per slab depth, FP32, FP64 local
+ * sums) and scored by the plain maximiser; the strict 26-neighbour maxima
+ * of its output planes are merged over all slabs (ttm_merge_peaks). The
+ * candidates and their order are those of ttm_find_peaks on the whole
+ * tomogram. The one difference is that the variance floor of Eq. 2
+ * (reading of zero variance) uses each slab's mean of g^2. The values
+ * differ by the rounding of the different FFT lengths.
+ *   d_field   float64 [K][tz][ty][tx] (device), params as for ttm_plan_create
+ *   h_idx, h_val  P entries (host): tomogram linear indices and map values
+ * Allocates the slab workspace (per call); synchronises `stream`. */
+ttm_status ttm_blocked_peaks(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                             const ttm_field_params* params, const float* h_tomo, int Z, int Y, int X, int slab_z,
+                             int map_kind, int P, double min_dist, int64_t* h_idx, float* h_val, int* h_count,
+                             void* stream);
+
 /* ------------------------------------------------------- step a6: Eqs. 1, 6, 7 */
 
 /* Classical template matching baseline: for every rotation q_j of h_quats

@@ -35,7 +35,7 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_
            "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
            "ttm_mlp_load", "ttm_plan_create_padded", "ttm_autotune_shape", "ttm_autotune_entries",
            "ttm_autotune_save", "ttm_autotune_load", "ttm_batch_create", "ttm_batch_run", "ttm_batch_work_shape",
-           "ttm_batch_destroy", "ttm_refine_peaks"]
+           "ttm_batch_destroy", "ttm_refine_peaks", "ttm_slab_ranges", "ttm_merge_peaks", "ttm_blocked_peaks"]
 
 
 class TTMError(RuntimeError):
@@ -92,6 +92,10 @@ def lib():
             "ttm_find_peaks_noalloc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _d, _vp, _vp, C.POINTER(_i), _vp]),
             "ttm_plan_fallback_count": (_i, [_vp, C.POINTER(_i64), _vp]),
             "ttm_refine_peaks": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp]),
+            "ttm_slab_ranges": (_i, [_i, _i, _i, _vp, _i]),
+            "ttm_merge_peaks": (_i, [_i64, _vp, _vp, _i, _i, _i, _i, _d, _vp, _vp]),
+            "ttm_blocked_peaks": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _d, _vp, _vp,
+                                       C.POINTER(_i), _vp]),
             "ttm_mlp_num_params": (_i64, [_i]),
             "ttm_mlp_create": (_i, [_vp, _i, C.c_uint64, C.POINTER(_vp)]),
             "ttm_mlp_destroy": (None, [_vp]),
@@ -466,6 +470,47 @@ def ttm_refine_peaks(plan: Plan, d_tmpl, d_orient, peaks, r_s: float = 3.0, stre
                                           float(r_s), idx.ctypes.data, quat.ctypes.data, lncc.ctypes.data,
                                           _stream(stream)))
     return idx[:P], quat[:P], lncc[:P]
+
+
+def ttm_slab_ranges(Z: int, tz: int, slab_z: int) -> np.ndarray:
+    """Block processing's z-slab table: rows (o0, o1, m0, m1, i0, i1)."""
+    n = lib().ttm_slab_ranges(int(Z), int(tz), int(slab_z), None, 0)
+    if n < 0:
+        raise ValueError("bad slab arguments")
+    out = np.zeros((max(n, 1), 6), dtype=np.int32)
+    lib().ttm_slab_ranges(int(Z), int(tz), int(slab_z), out.ctypes.data, n)
+    return out[:n]
+
+
+def ttm_merge_peaks(idx, val, shape, P: int, min_dist: float):
+    """Merge Peaks: (value desc, index asc) order, greedy exclusion at min_dist."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    val = np.ascontiguousarray(val, dtype=np.float32)
+    Z, Y, X = shape
+    oi = np.zeros(max(P, 1), dtype=np.int64)
+    ov = np.zeros(max(P, 1), dtype=np.float32)
+    n = lib().ttm_merge_peaks(idx.size, idx.ctypes.data, val.ctypes.data, Z, Y, X, int(P), float(min_dist),
+                              oi.ctypes.data, ov.ctypes.data)
+    if n < 0:
+        raise ValueError("bad merge arguments")
+    return oi[:n], ov[:n]
+
+
+def ttm_blocked_peaks(ctx: Context, d_field, p: ttm_field_params, tomo, slab_z: int, P: int, min_dist: float,
+                      map_kind: int = 0, stream=None):
+    """Block processing (Sec. 3.4) of a host tomogram (float32 numpy array)."""
+    import torch
+    tomo = np.ascontiguousarray(tomo, dtype=np.float32)
+    Z, Y, X = tomo.shape
+    K, tz, ty, tx = d_field.shape
+    idx = np.zeros(max(P, 1), dtype=np.int64)
+    val = np.zeros(max(P, 1), dtype=np.float32)
+    n = C.c_int(0)
+    ctx.check(lib().ttm_blocked_peaks(ctx.h, _dev(d_field, torch.float64, "d_field"), tz, ty, tx, C.byref(p),
+                                      tomo.ctypes.data, Z, Y, X, int(slab_z), int(map_kind), int(P),
+                                      float(min_dist), idx.ctypes.data, val.ctypes.data, C.byref(n),
+                                      _stream(stream)))
+    return idx[:n.value], val[:n.value]
 
 
 def ttm_find_peaks_noalloc(ctx: Context, d_map, box, P: int, min_dist: float, stream=None):

@@ -77,3 +77,50 @@ def test_rotation_set_rejects_bad_args():
     L = ttm.lib()
     assert L.ttm_rotation_set(0, 1, None) == 1
     assert L.ttm_rotation_set(4, 1, None) == 1
+
+
+# ------------------------------------------- block processing, host logic --
+
+@pytest.mark.parametrize("Z,tz,slab", [(40, 12, 5), (40, 12, 29), (40, 12, 100), (37, 11, 4), (12, 12, 3),
+                                       (64, 16, 1)])
+def test_slab_ranges_partition_and_halos(Z, tz, slab):
+    """Sec. 3.4 block processing: the output planes of the slabs partition
+    the valid planes; each slab's map planes are its output planes plus one
+    valid neighbour plane each side; its input covers every map plane's
+    template window and one filter plane beyond it (or reaches the tomogram
+    edge)."""
+    r = ttm.ttm_slab_ranges(Z, tz, slab)
+    cz = tz // 2
+    vz0, vz1 = cz, Z - (tz - cz) + 1
+    assert len(r) == -(-(vz1 - vz0) // slab)
+    covered = []
+    for o0, o1, m0, m1, i0, i1 in r:
+        covered += list(range(o0, o1))
+        assert m0 == max(vz0, o0 - 1) and m1 == min(vz1, o1 + 1)
+        lo = m0 - cz                       # first plane of the first window
+        hi = (m1 - 1) + (tz - 1 - cz)      # last plane of the last window
+        assert i0 == 0 or i0 <= lo - 1
+        assert i1 == Z or i1 >= hi + 2
+        assert 0 <= i0 < i1 <= Z and i1 - i0 >= tz
+    assert covered == list(range(vz0, vz1))
+    assert ttm.lib().ttm_slab_ranges(Z, Z + 1, slab, None, 0) == -1
+
+
+def test_merge_peaks_matches_greedy_definition():
+    rng = np.random.default_rng(12)
+    shape = (20, 30, 40)
+    n = 3000
+    idx = rng.choice(int(np.prod(shape)), n, replace=False).astype(np.int64)
+    val = np.round(rng.normal(size=n), 2).astype(np.float32)   # many equal values: the index breaks ties
+    got_i, got_v = ttm.ttm_merge_peaks(idx, val, shape, 60, 4.5)
+    order = sorted(range(n), key=lambda k: (-float(val[k]), int(idx[k])))
+    zyx = np.stack(np.unravel_index(idx, shape), axis=1).astype(float)
+    acc = []
+    for k in order:
+        if len(acc) == 60:
+            break
+        if all(np.sum((zyx[k] - zyx[a]) ** 2) >= 4.5 ** 2 for a in acc):
+            acc.append(k)
+    assert list(got_i) == [int(idx[k]) for k in acc]
+    assert np.array_equal(got_v, val[acc])
+    assert len(ttm.ttm_merge_peaks(idx[:0], val[:0], shape, 10, 3.0)[0]) == 0
