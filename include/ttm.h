@@ -171,7 +171,8 @@ void ttm_plan_valid_box(const ttm_plan* plan, int* box6);
  * through FFTs (periodic on the Z x Y x X grid), and the local normaliser
  * of Eq. 2: w = 1/sqrt(S2 - S1^2/M), S1 = sum m g(x+.), S2 = sum m^2
  * g(x+.)^2, summed in FP64; w = 0 where the local variance is zero to
- * rounding: at most 1e-12 * M * mean(g^2) or at most 1e-10 * S2.
+ * rounding: at most 1e-8 * M * mean(g^2) (a window too empty for the FP32
+ * correlation to resolve) or at most 1e-10 * S2.
  *   d_tomo  float32 [Z][Y][X] (device)
  *   d_C     float32 [K][Z][Y][X] output (device) */
 ttm_status ttm_correlate(ttm_plan* plan, const float* d_tomo, float* d_C, void* stream);

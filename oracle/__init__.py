@@ -221,9 +221,10 @@ def mean_square(g) -> float:
 
 
 def var_floor(g, M: float) -> float:
-    """Local variances at or below this give w = 0: 1e-12 * M * mean(g^2), the
-    level of an (almost) empty window relative to the volume's energy."""
-    return 1e-12 * M * mean_square(g)
+    """Local variances at or below this give w = 0: 1e-8 * M * mean(g^2), the
+    level of an (almost) empty window relative to the volume's energy, where
+    the LNCC of an FP32 correlation is not resolved."""
+    return 1e-8 * M * mean_square(g)
 
 
 def _vox(vox, shape):

@@ -27,7 +27,8 @@
  *   - rotated copies are t'_R(p) = t'(R^T p), trilinear, zero outside the grid;
  *   - with d' = 3 the tensor weight of a rotation R is (R e_z)^{(x)n};
  *   - w(x) = 0 where the local variance is not above var_floor (callers use
- *     1e-12 * M * mean(g^2)) or not above 1e-10 * S2.
+ *     1e-8 * M * mean(g^2): below it an FP32 correlation cannot resolve the
+ *     window, see the local normaliser) or not above 1e-10 * S2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -370,7 +371,11 @@ ORACLE_API int oracle_tensor_field(const double* tp, int tz, int ty, int tx, con
  * S2 = sum_p m(p)^2 g(x+p)^2, var = S2 - S1^2 / M, where g = h * f is the
  * filtered tomogram. The local variance is taken as zero (w = 0) where it is
  * not above var_floor or not above 1e-10 * S2, i.e. where the window is
- * constant to about five digits. Evaluated at the voxels listed in vox
+ * constant to about five digits. The callers' var_floor, 1e-8 M mean(g^2),
+ * marks windows that hold almost none of the volume's energy (a sliver of
+ * an object in an empty background): there 1/sqrt(var) would amplify the
+ * rounding of an FP32 correlation (about 1e-6 of its scale) past the
+ * value range of an LNCC. Evaluated at the voxels listed in vox
  * (linear indices); periodic != 0 wraps x+p around the grid, otherwise
  * samples outside the volume count as 0.                                     */
 

@@ -3,8 +3,9 @@
 //   G = FFT(g) in FP32 (the image spectrum of Alg. 2),
 //   S1 = m * g and S2 = m^2 * g^2 (Eq. 2) by one packed FP64 complex FFT of
 //   g + i g^2 against the real, even spectrum of the mask, and
-//   w = 1 / sqrt(S2 - S1^2 / M) (0 where the local variance is zero to
-//   rounding: below 1e-12 M mean(g^2) or below 1e-10 S2).
+//   w = 1 / sqrt(S2 - S1^2 / M) (0 where the local variance is below
+//   1e-8 M mean(g^2), a window too empty for the FP32 correlation to
+//   resolve, or below 1e-10 S2, constant to rounding).
 #include <cmath>
 #include <vector>
 
@@ -117,7 +118,7 @@ k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, i
     }
 }
 
-// floor = 1e-12 * M * mean(g^2) (fixed summation order)
+// floor = 1e-8 * M * mean(g^2) (fixed summation order)
 __global__ void __launch_bounds__(1024)
 k_var_floor(const double* __restrict__ partials, int64_t nblk, int64_t V, double M, double* floor_out)
 {
@@ -130,7 +131,7 @@ k_var_floor(const double* __restrict__ partials, int64_t nblk, int64_t V, double
         if (threadIdx.x < h) s2[threadIdx.x] += s2[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) floor_out[0] = 1e-12 * M * (s2[0] / (double)V);
+    if (threadIdx.x == 0) floor_out[0] = 1e-8 * M * (s2[0] / (double)V);
 }
 
 // mask placed at the origin of the Z x Y x X grid (wrapped), as real rows
