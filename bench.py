@@ -596,6 +596,89 @@ def run_blocked(args):
     print(json.dumps(line), flush=True)
 
 
+def run_study(args):
+    """Synthetic accuracy study (the analogue of Sec. 5.1, Tabs. 1-2 and the
+    SNR sweep): for each template (six-Gaussian blob, cylinder, L-shape;
+    21^3, r = 9), a tomogram with a 5 x 5 x 5 grid of 125 copies at uniform
+    random rotations, noise-free or with white noise at SNR 1 and 0.1; the
+    quaternion form (d' = 4) at n = 2 and 4; the 125 highest peaks of the
+    Frobenius map at exclusion 2r (TTM), then TTM-ref (r_s = 3). Each planted
+    copy is matched to the nearest peak within 6 voxels. Position error is
+    the Euclidean distance in voxels; rotation error 2 acos |q . q0| in
+    degrees, except for the cylinder, whose roll is undefined: the angle
+    between the axes R e_z."""
+    import torch
+    from paper_2408_02398_gb300 import build, synth
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    import oracle as O
+    dev = torch.device("cuda", 0)
+    ctx = ttm.Context(0)
+    N, r = 21, 9.0
+    templates = {"blob6": synth.gaussian_blob_template(N, seed=11), "cylinder": synth.cylinder_template(N),
+                 "l_shape": synth.l_shape_template(N)}
+    rows = []
+    t_start = time.perf_counter()
+    for name, tmpl in templates.items():
+        tmpl = tmpl.astype(np.float32)
+        t = torch.as_tensor(tmpl, device=dev)
+        for n in (2, 4):
+            p = ttm.params(order_n=n, mask_radius=r, n_rot_base=2048, dprime=4)
+            K = ttm.ttm_num_components(n, 4)
+            field = torch.empty((K, N, N, N), dtype=torch.float64, device=dev)
+            ttm.ttm_build_tensor_field(ctx, t, p, field)
+            for snr in (None, 1.0, 0.1):
+                vol, pl = synth.grid_tomogram(tmpl, 5, 26, 6, 31, snr, r)
+                shape = vol.shape
+                plan = ttm.Plan(ctx, field, p, shape, work_shape=ttm.ttm_autotune_shape(ctx, shape))
+                Zw, Yw, Xw = plan.shape
+                C = torch.empty((K, Zw, Yw, Xw), device=dev)
+                score = torch.empty((Zw, Yw, Xw), device=dev)
+                q = torch.empty((4, Zw, Yw, Xw), device=dev)
+                F = torch.empty((Zw, Yw, Xw), device=dev)
+                ttm.ttm_correlate(plan, torch.as_tensor(vol, device=dev), C)
+                ttm.ttm_peak_map(plan, C, score, q, F)
+                pk, _ = ttm.ttm_find_peaks(plan, F, 125, 2 * r)
+                ridx, rq, _ = ttm.ttm_refine_peaks(plan, t, q, pk, 3.0)
+                qmap = q.reshape(4, -1)[:, torch.as_tensor(pk, device=dev)].cpu().numpy().T
+
+                def zyx(i):
+                    return np.stack([i // (Yw * Xw), (i // Xw) % Yw, i % Xw], axis=1).astype(float)
+
+                def rot_err(qa, q0):
+                    if len(qa) == 0:
+                        return np.zeros(0)
+                    if name == "cylinder":
+                        a = np.array([O.quat_to_rot(v)[:, 2] for v in qa])
+                        b = np.array([O.quat_to_rot(v)[:, 2] for v in q0])
+                        return np.degrees(np.arccos(np.clip(np.abs(np.sum(a * b, 1)), 0, 1)))
+                    return np.degrees(2 * np.arccos(np.clip(np.abs(np.sum(qa * q0, 1)), 0, 1)))
+
+                row = {"template": name, "n": n, "snr": snr if snr is not None else "inf"}
+                for tag, pos, qq in (("ttm", zyx(pk), qmap), ("ttm_ref", zyx(ridx), rq)):
+                    d = np.linalg.norm(pos[None, :, :] - np.asarray(pl.centres, float)[:, None, :], axis=2)
+                    j = np.argmin(d, axis=1)
+                    ok = d[np.arange(len(j)), j] <= 6.0
+                    pe = d[np.arange(len(j)), j][ok]
+                    re = rot_err(qq[j[ok]], np.asarray(pl.quats)[ok])
+                    row[tag] = {"found": int(ok.sum()), "pos_mean": float(pe.mean()) if ok.any() else None,
+                                "pos_max": float(pe.max()) if ok.any() else None,
+                                "rot_mean_deg": float(re.mean()) if ok.any() else None,
+                                "rot_max_deg": float(re.max()) if ok.any() else None}
+                rows.append(row)
+                del plan, C, score, q, F
+    key = next(rw for rw in rows if rw["template"] == "blob6" and rw["n"] == 4 and rw["snr"] == "inf")
+    line = {"metric": "TTM-ref mean rotation error, noise-free, n = 4 (synthetic study)",
+            "value": key["ttm_ref"]["rot_mean_deg"], "unit": "deg", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "ttm_study_grid125_t21", "tomogram": "137^3, 5x5x5 copies",
+                                            "templates": list(templates), "dprime": 4, "orders": [2, 4],
+                                            "snr": ["inf", 1.0, 0.1], "rotations_field": 24 * 2048,
+                                            "r_s": 3.0},
+            "rows": rows, "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Order 6 on the same 1024 x 1024 x 256 volume: the network is trained
     on 10^6 (C / ||C||_F, plain maximiser direction) pairs from a separate
@@ -791,7 +874,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--localsum", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the local sums of Eq. 2")
-    ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched", "quaternion", "blocked"],
+    ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched", "quaternion", "blocked", "study"],
                     help="order4: the default plain FP32 workload; the others time one form against it")
     ap.add_argument("--zyx", default="", help="Z,Y,X of a smaller order-4 volume (profiling captures)")
     ap.add_argument("--crop-voxels", type=int, default=200)
@@ -811,6 +894,8 @@ def main():
         run_quaternion(args)
     elif args.workload == "blocked":
         run_blocked(args)
+    elif args.workload == "study":
+        run_study(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

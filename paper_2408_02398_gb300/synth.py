@@ -156,6 +156,72 @@ def gaussian_blob_template(n: int, seed: int, n_blobs: int = 6, centre_radius: f
     return out / out.max()
 
 
+def _smooth_step(d: np.ndarray, width: float) -> np.ndarray:
+    """1 inside (d <= 0), 0 outside, a raised-cosine edge of the given width."""
+    t = np.clip(d / width + 0.5, 0.0, 1.0)
+    return 0.5 * (1.0 + np.cos(math.pi * t))
+
+
+def cylinder_template(n: int, radius: float = 3.0, half_length: float = 7.0, edge: float = 1.5) -> np.ndarray:
+    """Cubic n^3 template: a solid cylinder along z through the centre with
+    soft edges (the simple shape of the synthetic study); max 1."""
+    c = n // 2
+    g = np.arange(n) - c
+    pz, py, px = np.meshgrid(g, g, g, indexing="ij")
+    rho = np.sqrt(px ** 2 + py ** 2)
+    out = _smooth_step(rho - radius, edge) * _smooth_step(np.abs(pz) - half_length, edge)
+    return out / out.max()
+
+
+def l_shape_template(n: int, thick: float = 2.0, long_arm: float = 8.0, short_arm: float = 5.0,
+                     edge: float = 1.5) -> np.ndarray:
+    """Cubic n^3 template: an L of two square bars of half-thickness thick,
+    one along +x (length long_arm) and one along +y (length short_arm) from a
+    common corner, shifted so that its centre of mass sits at the template
+    centre. Unequal arms leave it without rotational symmetry. Max 1."""
+    c = n // 2
+    g = np.arange(n) - c
+    pz, py, px = np.meshgrid(g, g, g, indexing="ij")
+
+    def bar(a, lo, hi, b1, b2):
+        return (_smooth_step(np.maximum(lo - a, a - hi), edge) * _smooth_step(np.abs(b1) - thick, edge)
+                * _smooth_step(np.abs(b2) - thick, edge))
+
+    def shape(dx, dy):
+        x, y = px - dx, py - dy
+        return np.maximum(bar(x, -thick, long_arm, y, pz), bar(y, -thick, short_arm, x, pz))
+
+    out = shape(0.0, 0.0)
+    m = out.sum()
+    cx, cy = float((out * px).sum() / m), float((out * py).sum() / m)
+    out = shape(-cx, -cy)
+    return out / out.max()
+
+
+def grid_tomogram(tmpl: np.ndarray, per_axis: int, spacing: int, margin: int, seed: int,
+                  snr: float | None, mask_radius: float):
+    """The synthetic study's tomogram: per_axis^3 copies of tmpl on a regular
+    grid (spacing voxels apart, margin voxels from the faces), each at a
+    Shoemake-uniform rotation, plus white noise at the given SNR (in-mask
+    variance of the copy / noise variance; None = noise-free). Returns
+    (float32 volume, Planted)."""
+    n = tmpl.shape[0]
+    edge = 2 * margin + (per_axis - 1) * spacing + n
+    shape = (edge, edge, edge)
+    c0 = margin + n // 2
+    ax = c0 + spacing * np.arange(per_axis)
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    centres = np.stack([zz.ravel(), yy.ravel(), xx.ravel()], axis=1)
+    quats = shoemake_quats(uniforms(seed, STREAM_ROT, 3 * len(centres)))
+    vol = np.zeros(shape)
+    plant(vol, np.asarray(tmpl, dtype=np.float64), centres, quats, 1.0)
+    if snr is not None:
+        m = sphere_mask_values(n, mask_radius)
+        sigma = math.sqrt(float(np.var(np.asarray(tmpl, dtype=np.float64)[m])) / float(snr))
+        vol += sigma * normals(seed, STREAM_NOISE, vol.size).reshape(shape)
+    return vol.astype(np.float32), Planted(centres, quats, 1.0)
+
+
 def lowpass_gaussian_periodic(vol: np.ndarray, sigma: float = 1.0, radius: int = 4) -> np.ndarray:
     """Separable periodic Gaussian low-pass (truncated at radius), used to
     colour the synthetic noise."""
