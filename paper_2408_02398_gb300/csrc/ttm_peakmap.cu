@@ -5,19 +5,22 @@
 //
 // One thread per voxel, components loaded structure-of-arrays (coalesced),
 // persistent CTAs. The form is evaluated at P = 128 fixed probe directions on
-// the half-sphere (p is even) as a tensor-core product per warp; the probe
-// values are kept in FP16 in shared memory, only to pick starts. The starts
-// are the best probe and, by angular suppression, up to NS - 1 more (NS = 2
-// for n = 2, 3 otherwise): the best probe farther than 20 degrees from the
-// starts already taken, if within 0.2 ||C||_F of the best. Each start gets
+// the half-sphere (p is even) as a tensor-core product per warp. The probes
+// form 16 cells of 8 neighbours, laid out so that one lane holds a whole
+// cell; only each cell's best probe is kept (a 16-bit key in shared
+// memory). The starts are the best probe and, by angular suppression, up to
+// NS - 1 more (NS = 2 for n = 2, 3 otherwise): the best cell best farther
+// than 20 degrees from the starts already taken, if within 0.2 ||C||_F of
+// the best. Each start gets
 // two interleaved Newton steps and the best is polished to convergence. The
 // derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
 // matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
 // is a Riemannian Newton step in a Householder tangent basis, limited to
 // 0.5 rad; where the tangent Hessian is not negative definite it is shifted
-// until it is (a Levenberg-Marquardt step), the step is halved until p does
-// not decrease, and a shifted power step (SS-HOPM, shift (n-1)||C||_F, never
-// decreasing) is the last resort.
+// until it is (a Levenberg-Marquardt direction) and the step is taken at the
+// full 0.5 rad, the step is halved until p does not decrease, and a shifted
+// power step (SS-HOPM, shift (n-1)||C||_F, never decreasing) is the last
+// resort.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -50,6 +53,12 @@ __host__ __device__ constexpr int kpad(int n) { return (ncomp3(n) + 3) / 4 * 4; 
 __host__ __device__ constexpr float factf(int n) { return n <= 1 ? 1.f : n * factf(n - 1); }
 // position of exponents (a, b, n-a-b) in graded-lex descending order
 __host__ __device__ constexpr int cidx(int n, int a, int b) { return (n - a) * (n - a + 1) / 2 + (n - a - b); }
+
+// probe cells: the 8 probes of cell c are the columns 2t, 2t+1 (t = c & 3)
+// of the 8-probe tensor-core tiles 4G .. 4G+3 (G = c >> 2), i.e. exactly
+// the columns one lane of a warp holds in those tiles
+constexpr int kCells = 128 / 8;
+__host__ __device__ constexpr int cell_row(int c, int m) { return ((c >> 2) * 4 + (m >> 1)) * 8 + 2 * (c & 3) + (m & 1); }
 
 // A = C . u^{N-2}: A_ij = sum_beta (N-2)!/beta! C_{e_i + e_j + beta} u^beta,
 // stored xx, xy, xz, yy, yz, zz
@@ -142,12 +151,16 @@ __device__ bool polish(const float* c, float frob, float& ux, float& uy, float& 
         // pure Newton where it is positive definite, else shift it to 0.05 ||C||_F
         const float mid = 0.5f * (h00 + h11), dif = 0.5f * (h00 - h11);
         const float lmin = mid - sqrtf(dif * dif + h01 * h01);
-        if (lmin <= 1e-6f * frob) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
+        const bool shifted = lmin <= 1e-6f * frob;
+        if (shifted) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
         const float idet = __frcp_rn(h00 * h11 - h01 * h01);
         float x0 = (h11 * g0 - h01 * g1) * idet;
         float x1 = (h00 * g1 - h01 * g0) * idet;
         const float xn2 = x0 * x0 + x1 * x1;
-        if (xn2 > 0.25f) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }  // |step| <= 0.5 rad
+        // |step| <= 0.5 rad; a shifted (not negative definite) step is taken
+        // at that full length: far from a maximum along a flat ridge the
+        // shifted step is tiny, and backtracking keeps p from decreasing
+        if (xn2 > 0.25f || (shifted && xn2 > 0.f)) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
         const float dx = x0 * b0x + x1 * b1x, dy = x0 * b0y + x1 * b1y, dz = x0 * b0z + x1 * b1z;
         bool moved = false;
         float t = 1.f;
@@ -216,11 +229,12 @@ __device__ __forceinline__ void newton_step_multi(const float* c, float frob, fl
         float h11 = N * p[s] - hN * (b1x * a1x + b1y * a1y + b1z * a1z);
         const float mid = 0.5f * (h00 + h11), dif = 0.5f * (h00 - h11);
         const float lmin = mid - sqrtf(dif * dif + h01 * h01);
-        if (lmin <= 1e-6f * frob) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
+        const bool shifted = lmin <= 1e-6f * frob;
+        if (shifted) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
         const float idet = __frcp_rn(h00 * h11 - h01 * h01);
         float x0 = (h11 * g0 - h01 * g1) * idet, x1 = (h00 * g1 - h01 * g0) * idet;
         const float xn2 = x0 * x0 + x1 * x1;
-        if (xn2 > 0.25f) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
+        if (xn2 > 0.25f || (shifted && xn2 > 0.f)) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
         d[s][0] = x0 * b0x + x1 * b1x;
         d[s][1] = x0 * b0y + x1 * b1y;
         d[s][2] = x0 * b0z + x1 * b1z;
@@ -272,16 +286,32 @@ struct ProbeTables {
     const __half* phi6h;
 };
 
-// probe values in shared memory as FP16 pairs: row p holds probes (2p, 2p+1)
-// of every thread's voxel, one 32-bit word per thread; the padding (136
-// words per row) keeps the fragment stores and loads of a warp in distinct
-// banks
+// one region of 32-bit words [row][kPvStride], column = thread: first the
+// staged FP16 input (pm_kx / 2 rows of component pairs), then the 16-bit
+// cell keys (cells 2r and 2r + 1 in the two halves of row r), so that every
+// warp only touches its own columns; the padding (136 words per row) keeps
+// the fragment loads and the key stores of a warp in distinct banks
 constexpr int kPvStride = kPmThreads + 8;
 __host__ __device__ constexpr int pm_kx(int n) { return (ncomp3(n) + 15) / 16 * 16; }
 __host__ __device__ constexpr int pm_kxs(int n) { return pm_kx(n) + 8; }
+__host__ __device__ constexpr int pm_rows(int n) { return pm_kx(n) / 2 > kCells / 2 ? pm_kx(n) / 2 : kCells / 2; }
 __host__ __device__ constexpr size_t pm_smem_bytes(int n)
 {
-    return sizeof(__half2) * (size_t)(kProbes / 2) * kPvStride + sizeof(__half) * (size_t)kProbes * pm_kxs(n);
+    return sizeof(uint32_t) * (size_t)pm_rows(n) * kPvStride + sizeof(__half) * (size_t)kProbes * pm_kxs(n);
+}
+// the 16-bit key of cell c of the voxel in column col
+__device__ __forceinline__ int pm_key_at(int c, int col) { return 2 * ((c >> 1) * kPvStride + col) + (c & 1); }
+// order-preserving 16-bit image of the FP16 rounding of v with the low 3
+// bits replaced by m (a cell member), and the value back
+__device__ __forceinline__ uint32_t pm_hkey(float v, uint32_t m)
+{
+    const uint32_t h = __half_as_ushort(__float2half_rn(v));
+    return ((h ^ ((h & 0x8000u) ? 0xFFFFu : 0x8000u)) & 0xFFF8u) | m;
+}
+__device__ __forceinline__ float pm_hkey_value(uint32_t k)
+{
+    const uint32_t h = (k & 0x8000u) ? (k ^ 0x8000u) : (~k & 0xFFFFu);
+    return __half2float(__ushort_as_half((unsigned short)h));
 }
 
 // which voxels a k_peakmap launch visits
@@ -319,11 +349,12 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
     constexpr int KXS = pm_kxs(N);
     constexpr int kStarts = nstarts(N);
     __shared__ float4 sdir[kProbes];
-    // pv: [kProbes][kPvStride] probe values / ||C||_F in FP16 (only used to
-    // pick starts); phih: [kProbes][KXS] FP16 weighted monomials
+    // xs / keys: the staged input, then the cell keys (see pm_key_at);
+    // phih: [kProbes][KXS] FP16 weighted monomials
     extern __shared__ __align__(16) __half pm_smem[];
-    __half2* pv = reinterpret_cast<__half2*>(pm_smem);
-    __half* phih = pm_smem + kProbes * kPvStride;
+    uint32_t* xs = reinterpret_cast<uint32_t*>(pm_smem);
+    uint16_t* keys = reinterpret_cast<uint16_t*>(pm_smem);
+    __half* phih = pm_smem + 2 * pm_rows(N) * kPvStride;
     {
         const __half* ph = N == 2 ? tabs.phi2h : (N == 4 ? tabs.phi4h : tabs.phi6h);
         const uint4* src = reinterpret_cast<const uint4*>(ph);
@@ -367,128 +398,136 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
         }
         const float F = sqrtf(F2);
         // Probe values p_j / ||C||_F of the warp's 32 voxels on the tensor
-        // cores: x = C / ||C||_F (|x_k| <= 1) is staged in FP16 transposed
-        // into this warp's own columns of pv (rows = components), loaded as
-        // A fragments, and [32 voxels x KX] x [KX x 128 probes] runs as
-        // m16n8k16 products with FP32 accumulation; the results overwrite
-        // the same columns of pv in FP16, and each voxel's maximum reaches
-        // its thread by quad shuffles.
-        float pmax = -INFINITY;
-        int jmax = 0;
+        // cores: x = C / ||C||_F (|x_k| <= 1) is staged in FP16 in this
+        // thread's column (rows = component pairs) and loaded as the A
+        // fragments of both 16-voxel tiles; every 8-probe B tile feeds both.
+        // Lane (g, t) holds columns 2t, 2t+1 of each tile for voxel rows g
+        // and g+8, so over four tiles it sees exactly the 8 probes of cell
+        // 4G + t and keeps their best (value, member) without shuffles; the
+        // cell bests go to shared memory as 16-bit keys.
         {
             const float invF = F > 0.f ? 1.f / F : 0.f;
 #pragma unroll
-            for (int k = 0; k < KX; k += 2)
-                pv[(k / 2) * kPvStride + threadIdx.x] =
-                    __floats2half2_rn(k < K ? c[k] * invF : 0.f, k + 1 < K ? c[k + 1] * invF : 0.f);
+            for (int k = 0; k < KX; k += 2) {
+                const __half2 h2 = __floats2half2_rn(k < K ? c[k] * invF : 0.f, k + 1 < K ? c[k + 1] * invF : 0.f);
+                xs[(k / 2) * kPvStride + threadIdx.x] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
             __syncwarp();
             const int g = lane >> 2, t = lane & 3;
-            const int col0 = warp * 32 + g;
-            // one m-tile (16 voxels = 16 columns) at a time: its outputs
-            // overwrite only its own columns, so the other tile's staged
-            // rows stay intact
-#pragma unroll 1
-            for (int mt = 0; mt < 2; mt++) {
-                const int col = col0 + 16 * mt;
-                uint32_t a[KX / 16][4];
+            uint32_t a[2][KX / 16][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
 #pragma unroll
                 for (int ks = 0; ks < KX / 16; ks++) {
-                    const __half2* r = pv + (8 * ks + t) * kPvStride + col;
-                    a[ks][0] = *reinterpret_cast<const uint32_t*>(r);
-                    a[ks][1] = *reinterpret_cast<const uint32_t*>(r + 8);
-                    a[ks][2] = *reinterpret_cast<const uint32_t*>(r + 4 * kPvStride);
-                    a[ks][3] = *reinterpret_cast<const uint32_t*>(r + 4 * kPvStride + 8);
+                    const uint32_t* r = xs + (8 * ks + t) * kPvStride + warp * 32 + 16 * mt + g;
+                    a[mt][ks][0] = r[0];
+                    a[mt][ks][1] = r[8];
+                    a[mt][ks][2] = r[4 * kPvStride];
+                    a[mt][ks][3] = r[4 * kPvStride + 8];
                 }
-                __syncwarp();
-                float mA = -INFINITY, mB = -INFINITY;
-                int iA = 0, iB = 0;
-#pragma unroll 2
-                for (int nt = 0; nt < kProbes / 8; nt++) {
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                    const __half* br = phih + (nt * 8 + g) * KXS + 2 * t;
+            __syncwarp();
+#pragma unroll 1
+            for (int G = 0; G < kCells / 4; G++) {
+                float mv[2][2];
+                uint32_t mi[2][2];
 #pragma unroll
-                    for (int ks = 0; ks < KX / 16; ks++)
-                        mma_f16(acc, a[ks], *reinterpret_cast<const uint32_t*>(br + 16 * ks),
-                                *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8));
-                    const int j0 = nt * 8 + 2 * t;
-                    pv[(j0 / 2) * kPvStride + col] = __floats2half2_rn(acc[0], acc[1]);
-                    pv[(j0 / 2) * kPvStride + col + 8] = __floats2half2_rn(acc[2], acc[3]);
-                    // running maximum and its probe (lowest index on ties)
-                    if (acc[0] > mA) { mA = acc[0]; iA = j0; }
-                    if (acc[1] > mA) { mA = acc[1]; iA = j0 + 1; }
-                    if (acc[2] > mB) { mB = acc[2]; iB = j0; }
-                    if (acc[3] > mB) { mB = acc[3]; iB = j0 + 1; }
+                for (int mt = 0; mt < 2; mt++) {
+                    mv[mt][0] = mv[mt][1] = -INFINITY;
+                    mi[mt][0] = mi[mt][1] = 0u;
                 }
 #pragma unroll
-                for (int o = 1; o <= 2; o <<= 1) {
-                    const float oA = __shfl_xor_sync(0xffffffffu, mA, o), oB = __shfl_xor_sync(0xffffffffu, mB, o);
-                    const int jA = __shfl_xor_sync(0xffffffffu, iA, o), jB = __shfl_xor_sync(0xffffffffu, iB, o);
-                    if (oA > mA || (oA == mA && jA < iA)) { mA = oA; iA = jA; }
-                    if (oB > mB || (oB == mB && jB < iB)) { mB = oB; iB = jB; }
+                for (int i = 0; i < 4; i++) {
+                    const __half* br = phih + ((4 * G + i) * 8 + g) * KXS + 2 * t;
+                    uint32_t b0[KX / 16], b1[KX / 16];
+#pragma unroll
+                    for (int ks = 0; ks < KX / 16; ks++) {
+                        b0[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks);
+                        b1[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8);
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < 2; mt++) {
+                        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int ks = 0; ks < KX / 16; ks++) mma_f16(acc, a[mt][ks], b0[ks], b1[ks]);
+                        if (acc[0] > mv[mt][0]) { mv[mt][0] = acc[0]; mi[mt][0] = 2 * i; }
+                        if (acc[1] > mv[mt][0]) { mv[mt][0] = acc[1]; mi[mt][0] = 2 * i + 1; }
+                        if (acc[2] > mv[mt][1]) { mv[mt][1] = acc[2]; mi[mt][1] = 2 * i; }
+                        if (acc[3] > mv[mt][1]) { mv[mt][1] = acc[3]; mi[mt][1] = 2 * i + 1; }
+                    }
                 }
-                // lane 16 mt + r owns row r: rows 0..7 sit in quad r (c0, c1),
-                // rows 8..15 in quad r - 8 (c2, c3)
-                const int r = lane - 16 * mt;
-                const int src = 4 * (r & 7);
-                const float vA = __shfl_sync(0xffffffffu, mA, src);
-                const float vB = __shfl_sync(0xffffffffu, mB, src);
-                const int kA = __shfl_sync(0xffffffffu, iA, src);
-                const int kB = __shfl_sync(0xffffffffu, iB, src);
-                if (r >= 0 && r < 16) {
-                    pmax = r < 8 ? vA : vB;
-                    jmax = r < 8 ? kA : kB;
+                const int cell = 4 * G + t, col = warp * 32 + g;
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++) {
+                    keys[pm_key_at(cell, col + 16 * mt)] = (uint16_t)pm_hkey(mv[mt][0], mi[mt][0]);
+                    keys[pm_key_at(cell, col + 16 * mt + 8)] = (uint16_t)pm_hkey(mv[mt][1], mi[mt][1]);
                 }
             }
             __syncwarp();
         }
-        // Starts by angular suppression: the best probe, then the best probe
-        // farther than kStartSepDeg from it, then the best one farther than
-        // that from both, each only if within kStartMargin ||C||_F of the best.
-        // Each extra start is one branch-free pass over the FP16 probe values
-        // masked by a precomputed 128-bit row of "far" probes.
-        const float thr = pmax - kStartMargin;
-        float sv[kStarts];
+        // Starts by angular suppression over the cell bests: the best probe,
+        // then the best cell best farther than kStartSepDeg from every start
+        // taken and within kStartMargin ||C||_F of the best. The first pass
+        // keeps the cells within the margin (an integer compare of keys) and
+        // farther than kStartSepDeg from the best; each later pass, over the
+        // kept cells only, drops those near the newest start.
         int sj[kStarts];
-#pragma unroll
-        for (int s = 0; s < kStarts; s++) { sv[s] = -INFINITY; sj[s] = 0; }
-        sv[0] = pmax;
-        sj[0] = jmax;
+        bool live[kStarts];
         {
-            uint4 far = __ldg(tabs.far + jmax);
+            uint32_t best = 0u;
+            int bc = 0;
 #pragma unroll
-            for (int s = 1; s < kStarts; s++) {
-                const uint32_t fw[4] = {far.x, far.y, far.z, far.w};
-                float bv = -INFINITY;
-                int bj = 0;
+            for (int cl = 0; cl < kCells; cl++) {
+                const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
+                if (kk > best) { best = kk; bc = cl; }
+            }
+            sj[0] = cell_row(bc, best & 7u);
+            live[0] = true;
 #pragma unroll
-                for (int w = 0; w < kProbes / 32; w++) {
+            for (int s = 1; s < kStarts; s++) { sj[s] = sj[0]; live[s] = false; }
+            const uint32_t thr = pm_hkey(pm_hkey_value(best) - kStartMargin, 0u);
+            uint32_t alive = 0u, bk = 0u;
+            int bcell = -1;
+            {
+                const float4 ds = sdir[sj[0]];
 #pragma unroll 4
-                    for (int bb = 0; bb < 32; bb += 2) {
-                        const float2 v = __half22float2(pv[(16 * w + bb / 2) * kPvStride + threadIdx.x]);
-                        if (((fw[w] >> bb) & 1u) && v.x > bv) { bv = v.x; bj = 32 * w + bb; }
-                        if (((fw[w] >> bb) & 2u) && v.y > bv) { bv = v.y; bj = 32 * w + bb + 1; }
+                for (int cl = 0; cl < kCells; cl++) {
+                    const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
+                    if (kk < thr) continue;
+                    const float4 dj = sdir[cell_row(cl, kk & 7u)];
+                    if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) < kStartSepCos) {
+                        alive |= 1u << cl;
+                        if (kk > bk) { bk = kk; bcell = cl; }
                     }
                 }
-                if (bv >= thr) {
-                    sv[s] = bv;
-                    sj[s] = bj;
-                    const uint4 f2 = __ldg(tabs.far + bj);
-                    far.x &= f2.x; far.y &= f2.y; far.z &= f2.z; far.w &= f2.w;
-                } else {
-                    break;
+            }
+#pragma unroll
+            for (int s = 1; s < kStarts; s++) {
+                if (bcell < 0) break;
+                sj[s] = cell_row(bcell, bk & 7u);
+                live[s] = true;
+                alive &= ~(1u << bcell);
+                if (s + 1 == kStarts) break;
+                const float4 ds = sdir[sj[s]];
+                bk = 0u;
+                bcell = -1;
+                for (uint32_t m = alive; m; m &= m - 1) {
+                    const int cl = __ffs((int)m) - 1;
+                    const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
+                    const float4 dj = sdir[cell_row(cl, kk & 7u)];
+                    if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) >= kStartSepCos) alive &= ~(1u << cl);
+                    else if (kk > bk) { bk = kk; bcell = cl; }
                 }
             }
         }
+        __syncwarp();  // the key rows are restaged by the next voxel block
         // two interleaved Newton steps from every start, then the full
         // polish of the best
         float best = 0.f, bx = 0.f, by = 0.f, bz = 1.f;
         if (F > 0.f) {
             float u[kStarts][3], ps[kStarts], A[kStarts][6];
-            bool live[kStarts];
 #pragma unroll
             for (int s = 0; s < kStarts; s++) {
-                live[s] = sv[s] > -INFINITY;
-                const float4 d = sdir[live[s] ? sj[s] : sj[0]];
+                const float4 d = sdir[sj[s]];
                 u[s][0] = d.x; u[s][1] = d.y; u[s][2] = d.z;
                 ps[s] = form_at<N>(c, d.x, d.y, d.z, A[s]);
             }
@@ -781,17 +820,42 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
 // ---------------------------------------------------------------- host --
 
 // probe directions (spherical Fibonacci on the half-sphere z > 0) and the
-// multiplicity-weighted monomials of each order, padded to float4 rows
+// multiplicity-weighted monomials of each order, padded to float4 rows. The
+// probes are grouped into kCells cells of 8 neighbours (each cell the
+// lowest-index unassigned probe and its 7 nearest unassigned ones, by
+// |d . d'|), member m of cell c stored at row cell_row(c, m).
 void build_probe_tables(std::vector<float>& out, size_t off[5])
 {
     const double ga = M_PI * (3.0 - std::sqrt(5.0));
-    std::vector<double> d(3 * kProbes);
+    std::vector<double> d0(3 * kProbes);
     for (int i = 0; i < kProbes; i++) {
         double z = (i + 0.5) / kProbes, r = std::sqrt(1.0 - z * z), ph = ga * i;
-        d[3 * i] = r * std::cos(ph);
-        d[3 * i + 1] = r * std::sin(ph);
-        d[3 * i + 2] = z;
+        d0[3 * i] = r * std::cos(ph);
+        d0[3 * i + 1] = r * std::sin(ph);
+        d0[3 * i + 2] = z;
     }
+    std::vector<int> order;
+    std::vector<char> used(kProbes, 0);
+    for (int seed = 0; seed < kProbes; seed++) {
+        if (used[seed]) continue;
+        std::vector<std::pair<double, int>> cand;
+        for (int j = 0; j < kProbes; j++)
+            if (!used[j])
+                cand.push_back({-std::fabs(d0[3 * seed] * d0[3 * j] + d0[3 * seed + 1] * d0[3 * j + 1] +
+                                           d0[3 * seed + 2] * d0[3 * j + 2]),
+                                j});
+        std::sort(cand.begin(), cand.end());
+        for (int m = 0; m < 8 && m < (int)cand.size(); m++) {
+            order.push_back(cand[m].second);
+            used[cand[m].second] = 1;
+        }
+    }
+    std::vector<double> d(3 * kProbes);
+    for (int c = 0; c < kCells; c++)
+        for (int m = 0; m < 8; m++) {
+            const int row = cell_row(c, m), j = order[8 * c + m];
+            for (int k = 0; k < 3; k++) d[3 * row + k] = d0[3 * j + k];
+        }
     out.clear();
     off[0] = 0;
     for (int i = 0; i < kProbes; i++) {
