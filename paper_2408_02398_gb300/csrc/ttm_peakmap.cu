@@ -11,8 +11,8 @@
 // memory). The starts are the best probe and, by angular suppression, up to
 // NS - 1 more (NS = 2 for n = 2, 3 otherwise): the best cell best farther
 // than 20 degrees from the starts already taken, if within 0.2 ||C||_F of
-// the best. Each start gets
-// two interleaved Newton steps and the best is polished to convergence. The
+// the best. The starts get up to two Newton steps each, in turn (one
+// inlined copy of the step), and the best is polished to convergence. The
 // derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
 // matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
 // is a Riemannian Newton step in a Householder tangent basis, limited to
@@ -103,17 +103,18 @@ __device__ __forceinline__ void normalise3(float& x, float& y, float& z)
     x *= s; y *= s; z *= s;
 }
 
-// up to ITERS polish steps of u towards a local maximum of p; p and A hold
+// up to iters polish steps of u towards a local maximum of p; p and A hold
 // the value and contraction at u on entry and on return. Returns whether
 // the tangent gradient fell below its tolerance.
-template <int N, int ITERS>
-__device__ bool polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p, float* A)
+template <int N>
+__device__ __forceinline__ bool polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p,
+                                       float* A, int iters)
 {
     const float tol_g2 = 1e-12f * frob * frob;  // |tangent gradient| <= 1e-6 ||C||_F
     const float tol_p = 1e-7f * frob;
     const float hN = (float)(N * (N - 1));
 #pragma unroll 1
-    for (int it = 0; it < ITERS; it++) {
+    for (int it = 0; it < iters; it++) {
         const float ax = A[0] * ux + A[1] * uy + A[2] * uz;
         const float ay = A[1] * ux + A[3] * uy + A[4] * uz;
         const float az = A[2] * ux + A[4] * uy + A[5] * uz;
@@ -189,86 +190,43 @@ __device__ bool polish(const float* c, float frob, float& ux, float& uy, float& 
     return false;
 }
 
-// One Newton step (as in polish) for NS starts at once: the starts are
-// independent, so their dependency chains interleave. A step is tried at
-// full and half length; if neither keeps p, a shifted power step is taken.
-template <int N, int NS>
-__device__ __forceinline__ void newton_step_multi(const float* c, float frob, float (*u)[3], float* p, float (*A)[6],
-                                                  const bool* live)
+// Largest eigenvalue of the symmetric 3x3 matrix A (xx, xy, xz, yy, yz, zz)
+// by the trigonometric form of the characteristic roots, and a unit
+// eigenvector: the longest cross product of two rows of A - lambda I (the
+// rows span the orthogonal complement of the eigenvector). Where A is a
+// multiple of I every direction is an eigenvector and e_z is returned.
+__device__ __forceinline__ float top_eig3(const float* A, float& ux, float& uy, float& uz)
 {
-    const float tol_p = 1e-7f * frob;
-    const float hN = (float)(N * (N - 1));
-    float d[NS][3];
-    bool moved[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        const float ux = u[s][0], uy = u[s][1], uz = u[s][2];
-        const float* a = A[s];
-        const float ax = a[0] * ux + a[1] * uy + a[2] * uz;
-        const float ay = a[1] * ux + a[3] * uy + a[4] * uz;
-        const float az = a[2] * ux + a[4] * uy + a[5] * uz;
-        const float fx = fabsf(ux), fy = fabsf(uy), fz = fabsf(uz);
-        const int kmax = (fx >= fy && fx >= fz) ? 0 : (fy >= fz ? 1 : 2);
-        const float vx = ux + (kmax == 0 ? (ux >= 0.f ? 1.f : -1.f) : 0.f);
-        const float vy = uy + (kmax == 1 ? (uy >= 0.f ? 1.f : -1.f) : 0.f);
-        const float vz = uz + (kmax == 2 ? (uz >= 0.f ? 1.f : -1.f) : 0.f);
-        const float r2 = __fdividef(2.f, vx * vx + vy * vy + vz * vz);
-        const float vj1 = kmax == 0 ? vy : vx, vj2 = kmax == 2 ? vy : vz;
-        const float b0x = (kmax != 0 ? 1.f : 0.f) - r2 * vj1 * vx, b0y = (kmax == 0 ? 1.f : 0.f) - r2 * vj1 * vy,
-                    b0z = -r2 * vj1 * vz;
-        const float b1x = -r2 * vj2 * vx, b1y = (kmax == 2 ? 1.f : 0.f) - r2 * vj2 * vy,
-                    b1z = (kmax != 2 ? 1.f : 0.f) - r2 * vj2 * vz;
-        const float g0 = N * (b0x * ax + b0y * ay + b0z * az);
-        const float g1 = N * (b1x * ax + b1y * ay + b1z * az);
-        const float a0x = a[0] * b0x + a[1] * b0y + a[2] * b0z, a0y = a[1] * b0x + a[3] * b0y + a[4] * b0z,
-                    a0z = a[2] * b0x + a[4] * b0y + a[5] * b0z;
-        const float a1x = a[0] * b1x + a[1] * b1y + a[2] * b1z, a1y = a[1] * b1x + a[3] * b1y + a[4] * b1z,
-                    a1z = a[2] * b1x + a[4] * b1y + a[5] * b1z;
-        float h00 = N * p[s] - hN * (b0x * a0x + b0y * a0y + b0z * a0z);
-        const float h01 = -hN * (b1x * a0x + b1y * a0y + b1z * a0z);
-        float h11 = N * p[s] - hN * (b1x * a1x + b1y * a1y + b1z * a1z);
-        const float mid = 0.5f * (h00 + h11), dif = 0.5f * (h00 - h11);
-        const float lmin = mid - sqrtf(dif * dif + h01 * h01);
-        const bool shifted = lmin <= 1e-6f * frob;
-        if (shifted) { const float sh = 0.05f * frob - lmin; h00 += sh; h11 += sh; }
-        const float idet = __frcp_rn(h00 * h11 - h01 * h01);
-        float x0 = (h11 * g0 - h01 * g1) * idet, x1 = (h00 * g1 - h01 * g0) * idet;
-        const float xn2 = x0 * x0 + x1 * x1;
-        if (xn2 > 0.25f || (shifted && xn2 > 0.f)) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
-        d[s][0] = x0 * b0x + x1 * b1x;
-        d[s][1] = x0 * b0y + x1 * b1y;
-        d[s][2] = x0 * b0z + x1 * b1z;
-        moved[s] = !live[s];
+    const float m = (A[0] + A[3] + A[5]) * (1.f / 3.f);
+    const float a = A[0] - m, b = A[3] - m, c = A[5] - m;
+    const float off = A[1] * A[1] + A[2] * A[2] + A[4] * A[4];
+    const float pp = (a * a + b * b + c * c + 2.f * off) * (1.f / 6.f);
+    ux = 0.f; uy = 0.f; uz = 1.f;
+    if (!(pp > 0.f)) return m;
+    const float sq = sqrtf(pp), is = 1.f / sq;
+    const float B00 = a * is, B11 = b * is, B22 = c * is, B01 = A[1] * is, B02 = A[2] * is, B12 = A[4] * is;
+    const float det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+    const float r = fminf(1.f, fmaxf(-1.f, 0.5f * det));
+    const float lam = m + 2.f * sq * cosf(acosf(r) * (1.f / 3.f));
+    const float a0 = A[0] - lam, a1 = A[1], a2 = A[2];  // row 0 of A - lambda I
+    const float b0 = A[1], b1 = A[3] - lam, b2 = A[4];  // row 1
+    const float c0 = A[2], c1 = A[4], c2 = A[5] - lam;  // row 2
+    float best = 0.f;
+    auto take = [&](float x0, float x1, float x2, float y0, float y1, float y2) {
+        const float cx = x1 * y2 - x2 * y1, cy = x2 * y0 - x0 * y2, cz = x0 * y1 - x1 * y0;
+        const float n2 = cx * cx + cy * cy + cz * cz;
+        if (n2 > best) { best = n2; ux = cx; uy = cy; uz = cz; }
+    };
+    take(a0, a1, a2, b0, b1, b2);
+    take(a0, a1, a2, c0, c1, c2);
+    take(b0, b1, b2, c0, c1, c2);
+    if (best > 0.f) {
+        const float s = rsqrtf(best);
+        ux *= s; uy *= s; uz *= s;
+    } else {
+        ux = 0.f; uy = 0.f; uz = 1.f;
     }
-#pragma unroll
-    for (int bt = 0; bt < 2; bt++) {
-        const float t = bt == 0 ? 1.f : 0.5f;
-#pragma unroll
-        for (int s = 0; s < NS; s++) {
-            float nx = u[s][0] + t * d[s][0], ny = u[s][1] + t * d[s][1], nz = u[s][2] + t * d[s][2];
-            normalise3(nx, ny, nz);
-            float An[6];
-            const float pn = form_at<N>(c, nx, ny, nz, An);
-            if (!moved[s] && pn >= p[s] - tol_p) {
-                u[s][0] = nx; u[s][1] = ny; u[s][2] = nz; p[s] = pn;
-#pragma unroll
-                for (int i = 0; i < 6; i++) A[s][i] = An[i];
-                moved[s] = true;
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        if (moved[s]) continue;
-        const float shift = (N - 1) * frob;
-        const float* a = A[s];
-        float nx = a[0] * u[s][0] + a[1] * u[s][1] + a[2] * u[s][2] + shift * u[s][0];
-        float ny = a[1] * u[s][0] + a[3] * u[s][1] + a[4] * u[s][2] + shift * u[s][1];
-        float nz = a[2] * u[s][0] + a[4] * u[s][1] + a[5] * u[s][2] + shift * u[s][2];
-        normalise3(nx, ny, nz);
-        u[s][0] = nx; u[s][1] = ny; u[s][2] = nz;
-        p[s] = form_at<N>(c, nx, ny, nz, A[s]);
-    }
+    return lam;
 }
 
 // probe tables: directions [kProbes][4] (x, y, z, 0) and weighted monomials
@@ -397,158 +355,179 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
             for (int k2 = K; k2 < KP; k2++) c[k2] = 0.f;
         }
         const float F = sqrtf(F2);
-        // Probe values p_j / ||C||_F of the warp's 32 voxels on the tensor
-        // cores: x = C / ||C||_F (|x_k| <= 1) is staged in FP16 in this
-        // thread's column (rows = component pairs) and loaded as the A
-        // fragments of both 16-voxel tiles; every 8-probe B tile feeds both.
-        // Lane (g, t) holds columns 2t, 2t+1 of each tile for voxel rows g
-        // and g+8, so over four tiles it sees exactly the 8 probes of cell
-        // 4G + t and keeps their best (value, member) without shuffles; the
-        // cell bests go to shared memory as 16-bit keys.
-        {
-            const float invF = F > 0.f ? 1.f / F : 0.f;
-#pragma unroll
-            for (int k = 0; k < KX; k += 2) {
-                const __half2 h2 = __floats2half2_rn(k < K ? c[k] * invF : 0.f, k + 1 < K ? c[k + 1] * invF : 0.f);
-                xs[(k / 2) * kPvStride + threadIdx.x] = *reinterpret_cast<const uint32_t*>(&h2);
+        float best = 0.f, bx = 0.f, by = 0.f, bz = 1.f;
+        if constexpr (N == 2) {
+            // n = 2: p(u) = u^T A u with A_ij = C_{e_i + e_j}, whose maximum
+            // over unit u is the top eigenpair of A; Newton polishes the
+            // closed form to FP32 convergence
+            if (F > 0.f) {
+                const float A2[6] = {c[0], c[1], c[2], c[3], c[4], c[5]};
+                top_eig3(A2, bx, by, bz);
+                float A[6];
+                best = form_at<N>(c, bx, by, bz, A);
+                polish<N>(c, F, bx, by, bz, best, A, kNewtonIters);
             }
-            __syncwarp();
-            const int g = lane >> 2, t = lane & 3;
-            uint32_t a[2][KX / 16][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int ks = 0; ks < KX / 16; ks++) {
-                    const uint32_t* r = xs + (8 * ks + t) * kPvStride + warp * 32 + 16 * mt + g;
-                    a[mt][ks][0] = r[0];
-                    a[mt][ks][1] = r[8];
-                    a[mt][ks][2] = r[4 * kPvStride];
-                    a[mt][ks][3] = r[4 * kPvStride + 8];
-                }
-            __syncwarp();
-#pragma unroll 1
-            for (int G = 0; G < kCells / 4; G++) {
-                float mv[2][2];
-                uint32_t mi[2][2];
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++) {
-                    mv[mt][0] = mv[mt][1] = -INFINITY;
-                    mi[mt][0] = mi[mt][1] = 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const __half* br = phih + ((4 * G + i) * 8 + g) * KXS + 2 * t;
-                    uint32_t b0[KX / 16], b1[KX / 16];
-#pragma unroll
-                    for (int ks = 0; ks < KX / 16; ks++) {
-                        b0[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks);
-                        b1[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8);
-                    }
-#pragma unroll
-                    for (int mt = 0; mt < 2; mt++) {
-                        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int ks = 0; ks < KX / 16; ks++) mma_f16(acc, a[mt][ks], b0[ks], b1[ks]);
-                        if (acc[0] > mv[mt][0]) { mv[mt][0] = acc[0]; mi[mt][0] = 2 * i; }
-                        if (acc[1] > mv[mt][0]) { mv[mt][0] = acc[1]; mi[mt][0] = 2 * i + 1; }
-                        if (acc[2] > mv[mt][1]) { mv[mt][1] = acc[2]; mi[mt][1] = 2 * i; }
-                        if (acc[3] > mv[mt][1]) { mv[mt][1] = acc[3]; mi[mt][1] = 2 * i + 1; }
-                    }
-                }
-                const int cell = 4 * G + t, col = warp * 32 + g;
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++) {
-                    keys[pm_key_at(cell, col + 16 * mt)] = (uint16_t)pm_hkey(mv[mt][0], mi[mt][0]);
-                    keys[pm_key_at(cell, col + 16 * mt + 8)] = (uint16_t)pm_hkey(mv[mt][1], mi[mt][1]);
-                }
-            }
-            __syncwarp();
-        }
-        // Starts by angular suppression over the cell bests: the best probe,
-        // then the best cell best farther than kStartSepDeg from every start
-        // taken and within kStartMargin ||C||_F of the best. The first pass
-        // keeps the cells within the margin (an integer compare of keys) and
-        // farther than kStartSepDeg from the best; each later pass, over the
-        // kept cells only, drops those near the newest start.
-        int sj[kStarts];
-        bool live[kStarts];
-        {
-            uint32_t best = 0u;
-            int bc = 0;
-#pragma unroll
-            for (int cl = 0; cl < kCells; cl++) {
-                const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
-                if (kk > best) { best = kk; bc = cl; }
-            }
-            sj[0] = cell_row(bc, best & 7u);
-            live[0] = true;
-#pragma unroll
-            for (int s = 1; s < kStarts; s++) { sj[s] = sj[0]; live[s] = false; }
-            const uint32_t thr = pm_hkey(pm_hkey_value(best) - kStartMargin, 0u);
-            uint32_t alive = 0u, bk = 0u;
-            int bcell = -1;
+        } else {
+            // Probe values p_j / ||C||_F of the warp's 32 voxels on the tensor
+            // cores: x = C / ||C||_F (|x_k| <= 1) is staged in FP16 in this
+            // thread's column (rows = component pairs) and loaded as the A
+            // fragments of both 16-voxel tiles; every 8-probe B tile feeds both.
+            // Lane (g, t) holds columns 2t, 2t+1 of each tile for voxel rows g
+            // and g+8, so over four tiles it sees exactly the 8 probes of cell
+            // 4G + t and keeps their best (value, member) without shuffles; the
+            // cell bests go to shared memory as 16-bit keys.
             {
-                const float4 ds = sdir[sj[0]];
-#pragma unroll 4
+                const float invF = F > 0.f ? 1.f / F : 0.f;
+    #pragma unroll
+                for (int k = 0; k < KX; k += 2) {
+                    const __half2 h2 = __floats2half2_rn(k < K ? c[k] * invF : 0.f, k + 1 < K ? c[k + 1] * invF : 0.f);
+                    xs[(k / 2) * kPvStride + threadIdx.x] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+                __syncwarp();
+                const int g = lane >> 2, t = lane & 3;
+                uint32_t a[2][KX / 16][4];
+    #pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+    #pragma unroll
+                    for (int ks = 0; ks < KX / 16; ks++) {
+                        const uint32_t* r = xs + (8 * ks + t) * kPvStride + warp * 32 + 16 * mt + g;
+                        a[mt][ks][0] = r[0];
+                        a[mt][ks][1] = r[8];
+                        a[mt][ks][2] = r[4 * kPvStride];
+                        a[mt][ks][3] = r[4 * kPvStride + 8];
+                    }
+                __syncwarp();
+    #pragma unroll 1
+                for (int G = 0; G < kCells / 4; G++) {
+                    float mv[2][2];
+                    uint32_t mi[2][2];
+    #pragma unroll
+                    for (int mt = 0; mt < 2; mt++) {
+                        mv[mt][0] = mv[mt][1] = -INFINITY;
+                        mi[mt][0] = mi[mt][1] = 0u;
+                    }
+    #pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const __half* br = phih + ((4 * G + i) * 8 + g) * KXS + 2 * t;
+                        uint32_t b0[KX / 16], b1[KX / 16];
+    #pragma unroll
+                        for (int ks = 0; ks < KX / 16; ks++) {
+                            b0[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks);
+                            b1[ks] = *reinterpret_cast<const uint32_t*>(br + 16 * ks + 8);
+                        }
+    #pragma unroll
+                        for (int mt = 0; mt < 2; mt++) {
+                            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+                            for (int ks = 0; ks < KX / 16; ks++) mma_f16(acc, a[mt][ks], b0[ks], b1[ks]);
+                            if (acc[0] > mv[mt][0]) { mv[mt][0] = acc[0]; mi[mt][0] = 2 * i; }
+                            if (acc[1] > mv[mt][0]) { mv[mt][0] = acc[1]; mi[mt][0] = 2 * i + 1; }
+                            if (acc[2] > mv[mt][1]) { mv[mt][1] = acc[2]; mi[mt][1] = 2 * i; }
+                            if (acc[3] > mv[mt][1]) { mv[mt][1] = acc[3]; mi[mt][1] = 2 * i + 1; }
+                        }
+                    }
+                    const int cell = 4 * G + t, col = warp * 32 + g;
+    #pragma unroll
+                    for (int mt = 0; mt < 2; mt++) {
+                        keys[pm_key_at(cell, col + 16 * mt)] = (uint16_t)pm_hkey(mv[mt][0], mi[mt][0]);
+                        keys[pm_key_at(cell, col + 16 * mt + 8)] = (uint16_t)pm_hkey(mv[mt][1], mi[mt][1]);
+                    }
+                }
+                __syncwarp();
+            }
+            // Starts by angular suppression over the cell bests: the best probe,
+            // then the best cell best farther than kStartSepDeg from every start
+            // taken and within kStartMargin ||C||_F of the best. The first pass
+            // keeps the cells within the margin (an integer compare of keys) and
+            // farther than kStartSepDeg from the best; each later pass, over the
+            // kept cells only, drops those near the newest start.
+            int sj[kStarts];
+            bool live[kStarts];
+            {
+                uint32_t best = 0u;
+                int bc = 0;
+    #pragma unroll
                 for (int cl = 0; cl < kCells; cl++) {
                     const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
-                    if (kk < thr) continue;
-                    const float4 dj = sdir[cell_row(cl, kk & 7u)];
-                    if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) < kStartSepCos) {
-                        alive |= 1u << cl;
-                        if (kk > bk) { bk = kk; bcell = cl; }
+                    if (kk > best) { best = kk; bc = cl; }
+                }
+                sj[0] = cell_row(bc, best & 7u);
+                live[0] = true;
+    #pragma unroll
+                for (int s = 1; s < kStarts; s++) { sj[s] = sj[0]; live[s] = false; }
+                const uint32_t thr = pm_hkey(pm_hkey_value(best) - kStartMargin, 0u);
+                uint32_t alive = 0u, bk = 0u;
+                int bcell = -1;
+                {
+                    const float4 ds = sdir[sj[0]];
+    #pragma unroll 4
+                    for (int cl = 0; cl < kCells; cl++) {
+                        const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
+                        if (kk < thr) continue;
+                        const float4 dj = sdir[cell_row(cl, kk & 7u)];
+                        if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) < kStartSepCos) {
+                            alive |= 1u << cl;
+                            if (kk > bk) { bk = kk; bcell = cl; }
+                        }
+                    }
+                }
+    #pragma unroll
+                for (int s = 1; s < kStarts; s++) {
+                    if (bcell < 0) break;
+                    sj[s] = cell_row(bcell, bk & 7u);
+                    live[s] = true;
+                    alive &= ~(1u << bcell);
+                    if (s + 1 == kStarts) break;
+                    const float4 ds = sdir[sj[s]];
+                    bk = 0u;
+                    bcell = -1;
+                    for (uint32_t m = alive; m; m &= m - 1) {
+                        const int cl = __ffs((int)m) - 1;
+                        const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
+                        const float4 dj = sdir[cell_row(cl, kk & 7u)];
+                        if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) >= kStartSepCos) alive &= ~(1u << cl);
+                        else if (kk > bk) { bk = kk; bcell = cl; }
                     }
                 }
             }
-#pragma unroll
-            for (int s = 1; s < kStarts; s++) {
-                if (bcell < 0) break;
-                sj[s] = cell_row(bcell, bk & 7u);
-                live[s] = true;
-                alive &= ~(1u << bcell);
-                if (s + 1 == kStarts) break;
-                const float4 ds = sdir[sj[s]];
-                bk = 0u;
-                bcell = -1;
-                for (uint32_t m = alive; m; m &= m - 1) {
-                    const int cl = __ffs((int)m) - 1;
-                    const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
-                    const float4 dj = sdir[cell_row(cl, kk & 7u)];
-                    if (fabsf(dj.x * ds.x + dj.y * ds.y + dj.z * ds.z) >= kStartSepCos) alive &= ~(1u << cl);
-                    else if (kk > bk) { bk = kk; bcell = cl; }
+            __syncwarp();  // the key rows are restaged by the next voxel block
+            // up to kPreIters Newton steps from every start in turn, then up to
+            // kNewtonIters on the best: one inlined copy of the step serves all
+            // of them (a small kernel body stays in the instruction cache)
+            if (F > 0.f) {
+                uint32_t rows = 0u;  // start rows, 7 bits each
+                int ns = 0;
+    #pragma unroll
+                for (int s = 0; s < kStarts; s++)
+                    if (live[s]) { rows |= (uint32_t)sj[s] << (7 * s); ns = s + 1; }
+                float bA[6], A[6];
+                const float4 d0 = sdir[rows & 127u];
+                float ux = d0.x, uy = d0.y, uz = d0.z;
+                float p = form_at<N>(c, ux, uy, uz, A);
+                best = -INFINITY;
+                int s = 0;
+    #pragma unroll 1
+                for (;;) {
+                    const bool final_polish = s == ns;
+                    polish<N>(c, F, ux, uy, uz, p, A, final_polish ? kNewtonIters : kPreIters);
+                    if (final_polish) break;
+                    if (p > best) {
+                        best = p; bx = ux; by = uy; bz = uz;
+    #pragma unroll
+                        for (int i = 0; i < 6; i++) bA[i] = A[i];
+                    }
+                    if (++s < ns) {
+                        const float4 d = sdir[(rows >> (7 * s)) & 127u];
+                        ux = d.x; uy = d.y; uz = d.z;
+                        p = form_at<N>(c, ux, uy, uz, A);
+                    } else {
+                        ux = bx; uy = by; uz = bz; p = best;
+    #pragma unroll
+                        for (int i = 0; i < 6; i++) A[i] = bA[i];
+                    }
                 }
+                best = p; bx = ux; by = uy; bz = uz;
             }
-        }
-        __syncwarp();  // the key rows are restaged by the next voxel block
-        // two interleaved Newton steps from every start, then the full
-        // polish of the best
-        float best = 0.f, bx = 0.f, by = 0.f, bz = 1.f;
-        if (F > 0.f) {
-            float u[kStarts][3], ps[kStarts], A[kStarts][6];
-#pragma unroll
-            for (int s = 0; s < kStarts; s++) {
-                const float4 d = sdir[sj[s]];
-                u[s][0] = d.x; u[s][1] = d.y; u[s][2] = d.z;
-                ps[s] = form_at<N>(c, d.x, d.y, d.z, A[s]);
-            }
-#pragma unroll 1
-            for (int it = 0; it < kPreIters; it++) newton_step_multi<N, kStarts>(c, F, u, ps, A, live);
-            int bs = 0;
-#pragma unroll
-            for (int s = 1; s < kStarts; s++)
-                if (live[s] && ps[s] > ps[bs]) bs = s;
-            float bA[6];
-            best = ps[0]; bx = u[0][0]; by = u[0][1]; bz = u[0][2];
-#pragma unroll
-            for (int i = 0; i < 6; i++) bA[i] = A[0][i];
-#pragma unroll
-            for (int s = 1; s < kStarts; s++)
-                if (s == bs) {
-                    best = ps[s]; bx = u[s][0]; by = u[s][1]; bz = u[s][2];
-#pragma unroll
-                    for (int i = 0; i < 6; i++) bA[i] = A[s][i];
-                }
-            polish<N, kNewtonIters>(c, F, bx, by, bz, best, bA);
         }
         // canonical half-sphere: last non-zero of (z, y, x) positive
         if (bz < 0.f || (bz == 0.f && (by < 0.f || (by == 0.f && bx < 0.f)))) { bx = -bx; by = -by; bz = -bz; }
@@ -758,7 +737,7 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
             else { ux = 0.f; uy = 0.f; uz = 1.f; }
             float A[6];
             best = form_at<N>(c, ux, uy, uz, A);
-            bool conv = polish<N, kNewtonIters>(c, F, ux, uy, uz, best, A);
+            bool conv = polish<N>(c, F, ux, uy, uz, best, A, kNewtonIters);
             // bound on every probe value: the best probe in FP32, the others
             // by the runner-up plus the FP16 error bound
             float pexact = 0.f;
@@ -776,7 +755,7 @@ k_peakmap_mlp(const float* __restrict__ C, int64_t V, float* __restrict__ score,
                 const float4 d = sdir[pj1];
                 float vx = d.x, vy = d.y, vz = d.z, A2[6];
                 float p2 = form_at<N>(c, vx, vy, vz, A2);
-                const bool conv2 = polish<N, kNewtonIters>(c, F, vx, vy, vz, p2, A2);
+                const bool conv2 = polish<N>(c, F, vx, vy, vz, p2, A2, kNewtonIters);
                 if (p2 > best) { best = p2; ux = vx; uy = vy; uz = vz; conv = conv2; }
             }
             // accepted only where the plain maximiser would itself use the
