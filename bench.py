@@ -278,7 +278,7 @@ def run_ours(args, ws, rank, local):
     roof = {"bound": "alu", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
             "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
             "peak_source": "FP32 FMA rate from unit counts at the sampled SM clock",
-            "traffic": 4.22e9, "flops_per_voxel": 2 * K * probes}
+            "traffic": 4.19e9, "flops_per_voxel": 2 * K * probes}
     roof["frac"] = roof["achieved"] / roof["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
     roof_corr = {"bound": "hbm", "kernel": "ttm_correlate (stages prefilter..xpass)",
