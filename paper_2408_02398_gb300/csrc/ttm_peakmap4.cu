@@ -52,7 +52,7 @@ namespace ttm {
 constexpr int kP4 = 512;                 // probes on the half 3-sphere
 constexpr int kP4Cells = kP4 / 8;        // one cell per 8-column MMA tile
 constexpr int kP4Threads = 256;
-constexpr int kP4Pre = 3;                // interleaved Newton steps per start
+constexpr int kP4Pre = 3;                // Newton steps per start (starts in turn)
 constexpr int kP4Polish = 12;            // Newton steps on the best start
 constexpr float kP4Margin = 0.2f;        // starts within this * ||C||_F of the best
 constexpr float kP4SepCos = 0.90630779f; // starts lie farther apart than 25 degrees
