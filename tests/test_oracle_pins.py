@@ -100,7 +100,7 @@ def test_component_counts_match_paper():
     assert [O.num_components(n, 3) for n in (2, 4, 6)] == [6, 15, 28]
 
 
-@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4)])
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4), (6, 4)])
 def test_multi_indices_enumerate_all_multisets(n, d):
     a = O.multi_indices(n, d)
     brute = {tuple(sum(1 for e in comb if e == i) for i in range(d))
@@ -114,7 +114,7 @@ def test_multi_indices_enumerate_all_multisets(n, d):
     assert m.sum() == pytest.approx(d ** n)
 
 
-@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (4, 4)])
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (4, 4), (6, 4)])
 def test_frobenius_of_tensor_power(n, d):
     rng = np.random.default_rng(1)
     v = rng.normal(size=d)
@@ -259,7 +259,7 @@ def test_field_exact_under_cube_quadrature(n):
     assert np.abs(T - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4)])
+@pytest.mark.parametrize("n,d", [(2, 3), (4, 3), (6, 3), (2, 4), (4, 4), (6, 4)])
 def test_field_of_constant_is_sphere_moment(n, d):
     """A constant t' is reproduced exactly by trilinear resampling away from
     the grid edge, so T_alpha there equals the quadrature of E[u^alpha] over
