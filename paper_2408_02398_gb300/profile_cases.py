@@ -1,0 +1,43 @@
+"""Small cases for kernel profiles (ncu captures), run as
+
+    python -m paper_2408_02398_gb300.profile_cases quaternion Z,Y,X REPS
+
+quaternion: a d' = 4 plan (n = 4, 16^3 template, r = 7, 24 x 64 field
+rotations) on a Z x Y x X white-noise tomogram; one correlation, then REPS
+timed calls of the quaternion maximiser (CUDA events), so that a capture of
+the maximiser kernel can skip the first call and take the next."""
+import sys
+
+import numpy as np
+
+
+def quaternion(shape, reps: int) -> float:
+    import torch
+    from . import build, synth
+    build.build()
+    from . import ttm
+    ctx = ttm.Context(0)
+    tmpl = synth.gaussian_blob_template(16, seed=5)
+    p = ttm.params(order_n=4, mask_radius=7.0, n_rot_base=64, dprime=4)
+    m = ttm.Matcher(ctx, tmpl, p, shape)
+    tomo = torch.as_tensor(synth.normals(3, 1, int(np.prod(shape))).reshape(shape).astype(np.float32), device="cuda")
+    m.run(tomo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ttm.ttm_peak_map(m.plan, m.C, m.score, m.orient, m.frob)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    print("peak map %.3f ms per call, %d voxels" % (ms, int(np.prod(shape))))
+    return ms
+
+
+if __name__ == "__main__":
+    case = sys.argv[1] if len(sys.argv) > 1 else "quaternion"
+    zyx = tuple(int(v) for v in (sys.argv[2] if len(sys.argv) > 2 else "64,256,256").split(","))
+    reps = int(sys.argv[3]) if len(sys.argv) > 3 else 3
+    if case != "quaternion":
+        raise SystemExit("unknown case %r" % case)
+    quaternion(zyx, reps)
