@@ -479,7 +479,7 @@ def run_quaternion(args):
         cen = np.array([(int(c[0]) * Y + int(c[1])) * X + int(c[2]) for c in wl.planted.centres])
         oc = orient.reshape(dp, -1)[:, torch.as_tensor(cen, device=dev)].cpu().numpy().T
         if dp == 3:
-            ez = np.array([O.quat_to_rot(q)[:, 2] for q in wl.planted.quats])
+            ez = np.array([synth.quat_matrix(q)[:, 2] for q in wl.planted.quats])
             ang3 = np.degrees(np.arccos(np.clip(np.abs(np.sum(oc * ez, axis=1)), 0, 1)))
         else:
             got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
@@ -611,7 +611,6 @@ def run_study(args):
     from paper_2408_02398_gb300 import build, synth
     build.build()
     from paper_2408_02398_gb300 import ttm
-    import oracle as O
     dev = torch.device("cuda", 0)
     ctx = ttm.Context(0)
     N, r = 21, 9.0
@@ -649,8 +648,8 @@ def run_study(args):
                     if len(qa) == 0:
                         return np.zeros(0)
                     if name == "cylinder":
-                        a = np.array([O.quat_to_rot(v)[:, 2] for v in qa])
-                        b = np.array([O.quat_to_rot(v)[:, 2] for v in q0])
+                        a = np.array([synth.quat_matrix(v)[:, 2] for v in qa])
+                        b = np.array([synth.quat_matrix(v)[:, 2] for v in q0])
                         return np.degrees(np.arccos(np.clip(np.abs(np.sum(a * b, 1)), 0, 1)))
                     return np.degrees(2 * np.arccos(np.clip(np.abs(np.sum(qa * q0, 1)), 0, 1)))
 
