@@ -82,12 +82,16 @@ def test_gloo_two_ranks_timing_and_merge_peaks():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     ws, port = 2, _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, ws, port, q)) for r in range(ws)]
+    procs = [ctx.Process(target=_worker, args=(r, ws, port, q), daemon=True) for r in range(ws)]
     for p in procs:
         p.start()
-    res = [q.get(timeout=240) for _ in range(ws)]
-    for p in procs:
-        p.join(timeout=60)
+    try:
+        res = [q.get(timeout=240) for _ in range(ws)]
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
     for r in res:
         assert r[1] != "error", r
     shape = (24, 20, 22)
