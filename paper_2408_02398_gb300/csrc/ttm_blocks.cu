@@ -10,7 +10,6 @@
 // whole tomogram.
 #include <algorithm>
 #include <map>
-#include <memory>
 #include <vector>
 
 #include "ttm_internal.h"
