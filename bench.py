@@ -682,7 +682,7 @@ def run_learned(args):
     """Order 6 on the same 1024 x 1024 x 256 volume: the network is trained
     on 10^6 (C / ||C||_F, plain maximiser direction) pairs from a separate
     seeded 160^3 tomogram with the same template, then the learned
-    maximiser is timed against the plain one on the big volume and judged
+    maximiser is timed against the plain one on the big volume and checked
     by it over every valid voxel."""
     import torch
     from paper_2408_02398_gb300 import build, synth
@@ -761,7 +761,7 @@ def run_learned(args):
             "learned": {"peak_map_ms": ms_learn, "correlate_ms": ms_corr, "train_s": train_s,
                         "final_batch_loss": loss, "fallback_voxels": fb, "fallback_frac": fb / V,
                         "kernel_launches_per_call": launches},
-            "judge": {"valid_voxels": nvalid, "violations_below_plain_1e-4": viol,
+            "check_vs_plain": {"valid_voxels": nvalid, "violations_below_plain_1e-4": viol,
                       "min_score_diff": float(d.min().item()), "max_score_diff": float(d.max().item()),
                       "orientation_deg_p99": float(torch.quantile(ang.flatten()[::97].float(), 0.99).item())},
             "vs_plain": {"whole_step": vl / vp, "peak_map": ms_plain / ms_learn},

@@ -1,7 +1,7 @@
 """Learned warm start on the GPU: the MLP's FP32 forward and gradient and its
 BF16 tensor-core inference against the FP64 oracle, training on pairs that
 the plain maximiser labels, and the learned maximiser against both the plain
-maximiser (the judge) and the oracle, including what it gains."""
+maximiser (the reference for its error) and the oracle, including what it gains."""
 import numpy as np
 import pytest
 
@@ -143,7 +143,7 @@ def test_training_reduces_loss(trained):
 
 
 def test_learned_never_below_plain(trained):
-    """The judge: over every valid voxel of the held-out tomogram the learned
+    """Error check: over every valid voxel of the held-out tomogram the learned
     score is not more than 1e-4 below the plain maximiser's."""
     M, b = trained["M"], trained["box"]
     d = (trained["sl"] - M.score)[b[0]:b[1], b[2]:b[3], b[4]:b[5]]
