@@ -124,3 +124,47 @@ def test_merge_peaks_matches_greedy_definition():
     assert list(got_i) == [int(idx[k]) for k in acc]
     assert np.array_equal(got_v, val[acc])
     assert len(ttm.ttm_merge_peaks(idx[:0], val[:0], shape, 10, 3.0)[0]) == 0
+
+
+C_MAIN = r"""
+#include "ttm.h"
+#include <stdio.h>
+int main(void)
+{
+    int rows[6 * 8];
+    int n = ttm_slab_ranges(40, 12, 5, rows, 8);
+    int64_t idx[2] = {5, 100};
+    float val[2] = {1.0f, 2.0f};
+    int64_t oi[2];
+    float ov[2];
+    int m = ttm_merge_peaks(2, idx, val, 10, 10, 10, 2, 1.0, oi, ov);
+    printf("%d %d %lld %d\n", n, m, (long long)oi[0], ttm_num_components(4, 4));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """include/ttm.h compiles as strict C99 and as C++17, and a C program
+    that calls the host-only entry points links against libttm.so."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    hdr = os.path.join(inc, "ttm.h")
+    for cmd in ([gcc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", hdr],
+                [shutil.which("g++") or "g++", "-fsyntax-only", "-x", "c++", "-std=c++17", "-Wall", "-Werror", hdr]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    src = tmp_path / "main.c"
+    src.write_text(C_MAIN)
+    lib_dir = os.path.join(ROOT, "paper_2408_02398_gb300")
+    exe = tmp_path / "main"
+    r = subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-L", lib_dir, "-lttm", "-Wl,-rpath," + lib_dir,
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["6", "2", "100", "35"]   # 29 valid planes in slabs of 5
