@@ -32,6 +32,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2408_02398_gb300 import synth  # noqa: E402  (seeded input generators only)
+
 WORKLOAD = "ttm_n4_512x512x200_t40_r16_300copies_snr0.1"
 METRIC = "TTM voxels/s (score+orientation map)"
 UNIT = "voxels/s"
@@ -169,14 +171,272 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------- GPU path --
 
+def _events(stream):
+    import torch
+    e = torch.cuda.Event(enable_timing=True)
+    e.record(stream)
+    return e
+
+
+def _step_ms(fn, steps, warmup, stream):
+    """Milliseconds per call of fn: CUDA events on `stream`, after warm-up."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = _events(stream)
+    for _ in range(steps):
+        fn()
+    e1 = _events(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def e2e_pipelined(ttm, m, h_tomo, steps, warmup, dev):
+    """End to end through the public calls with host buffers, copies inside
+    the timed region: per step the pinned tomogram goes to the device
+    (copy stream), ttm_correlate + ttm_peak_map run (compute stream) and the
+    score and orientation maps come back to pinned host memory (copy-out
+    stream). Two buffer sets let step i+1's upload and step i-1's download
+    overlap step i's kernels; events order every reuse of a buffer."""
+    import torch
+    Z, Y, X = h_tomo.shape
+    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    d_in = [torch.empty((Z, Y, X), device=dev) for _ in range(2)]
+    d_s = [torch.empty((Z, Y, X), device=dev) for _ in range(2)]
+    d_o = [torch.empty((3, Z, Y, X), device=dev) for _ in range(2)]
+    h_s = [torch.empty((Z, Y, X)).pin_memory() for _ in range(2)]
+    h_o = [torch.empty((3, Z, Y, X)).pin_memory() for _ in range(2)]
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    in_ready, in_free, maps_ready, maps_free = ([ev(), ev()] for _ in range(4))
+    for e in in_free + maps_free:
+        e.record(s_cmp)
+
+    def step(i):
+        b = i % 2
+        s_in.wait_event(in_free[b])
+        with torch.cuda.stream(s_in):
+            d_in[b].copy_(h_tomo, non_blocking=True)
+        in_ready[b].record(s_in)
+        s_cmp.wait_event(in_ready[b])
+        s_cmp.wait_event(maps_free[b])
+        ttm.ttm_correlate(m.plan, d_in[b], m.C, stream=s_cmp)
+        in_free[b].record(s_cmp)
+        ttm.ttm_peak_map(m.plan, m.C, d_s[b], d_o[b], stream=s_cmp)
+        maps_ready[b].record(s_cmp)
+        s_out.wait_event(maps_ready[b])
+        with torch.cuda.stream(s_out):
+            h_s[b].copy_(d_s[b], non_blocking=True)
+            h_o[b].copy_(d_o[b], non_blocking=True)
+        maps_free[b].record(s_out)
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s_in)
+    for i in range(steps):
+        step(i)
+    s_in.wait_stream(s_out)
+    t1.record(s_in)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
+def tm_comparator(ttm, ctx, wl, p, dev, n_rot):
+    """Classical per-rotation TM (tm_correlate) on the same volume over
+    n_rot rotations taken evenly from the 45 123-rotation super-Fibonacci
+    list (the count the paper cites for a 7-degree step, Sec. 1). One call
+    is timed on the host around its synchronising return; the library's
+    per-call set-up (workspace, image preparation) is amortised over the
+    rotations."""
+    import torch
+    full = ttm.ttm_rotation_set(45123, cube=False)
+    sel = full[np.linspace(0, full.shape[0] - 1, n_rot).astype(np.int64)]
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    t = torch.as_tensor(wl.template, device=dev)
+    best = torch.empty(wl.tomo.shape, device=dev)
+    idx = torch.empty(wl.tomo.shape, dtype=torch.int32, device=dev)
+    ttm.tm_correlate(ctx, d_tomo, t, p, sel[:4], best, idx)     # warm-up (kernels, allocator)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ttm.tm_correlate(ctx, d_tomo, t, p, sel, best, idx)
+    torch.cuda.synchronize()
+    s = time.perf_counter() - t0
+    return {"rotations_timed": int(n_rot), "ms_per_rotation": 1e3 * s / n_rot,
+            "implied_45123_rotations_s": s / n_rot * 45123.0}
+
+
+def cufft_comparator(ttm, m, wl, dev, steps):
+    """The same correlation through cuFFT (torch.fft), timed only:
+    G = rfftn(g), then for each of the K components irfftn(G conj(T_hat))
+    times w, written into a K x V map; and the local sums of Eq. 2 as FP64
+    cuFFT transforms of g and g^2 against the mask spectrum. g (the 3-tap
+    filter), w and the template spectra are prepared outside the timed
+    region, as the library's plan holds its spectra."""
+    import torch
+    Z, Y, X = wl.tomo.shape
+    K = m.C.shape[0]
+    f = torch.as_tensor(wl.tomo, device=dev)[None, None]
+    a = 0.2
+    taps = torch.tensor([a, 1 - 2 * a, a], device=dev)
+    g = f
+    for ax in range(3):
+        shape = [1, 1, 1, 1, 1]
+        shape[2 + ax] = 3
+        pad = [0, 0, 0]
+        pad[ax] = 1
+        g = torch.nn.functional.conv3d(g, taps.reshape(shape), padding=tuple(pad))
+    g = g[0, 0].contiguous()
+    w = torch.empty((Z, Y, X), device=dev)
+    ttm.ttm_plan_copy_w(m.plan, w)
+    tz, ty, tx = m.field.shape[1:]
+    Tg = torch.zeros((K, Z, Y, X), dtype=torch.float32, device=dev)
+    cz, cy, cx = tz // 2, ty // 2, tx // 2
+    # place each component at the origin of the working grid (wrapped)
+    zi = torch.tensor([(d - cz) % Z for d in range(tz)], device=dev)
+    yi = torch.tensor([(d - cy) % Y for d in range(ty)], device=dev)
+    xi = torch.tensor([(d - cx) % X for d in range(tx)], device=dev)
+    Tg[:, zi[:, None, None], yi[None, :, None], xi[None, None, :]] = m.field.float()
+    That = torch.fft.rfftn(Tg, dim=(1, 2, 3))
+    del Tg
+    out = torch.empty((K, Z, Y, X), device=dev)
+    mk = torch.zeros((Z, Y, X), dtype=torch.float64, device=dev)
+    msk = torch.as_tensor(synth.sphere_mask_values(tz, wl.mask_radius), dtype=torch.float64, device=dev)
+    mk[zi[:, None, None], yi[None, :, None], xi[None, None, :]] = msk
+    Mhat = torch.fft.rfftn(mk)
+    M = float(msk.sum())
+    stream = torch.cuda.current_stream()
+
+    def corr():
+        G = torch.fft.rfftn(g)
+        for k in range(K):
+            torch.mul(torch.fft.irfftn(G * That[k].conj(), s=(Z, Y, X)), w, out=out[k])
+
+    def lsum():
+        gd = g.double()
+        S1 = torch.fft.irfftn(torch.fft.rfftn(gd) * Mhat.conj(), s=(Z, Y, X))
+        S2 = torch.fft.irfftn(torch.fft.rfftn(gd * gd) * Mhat.conj(), s=(Z, Y, X))
+        var = S2 - S1 * S1 / M
+        return var
+
+    ms_corr = _step_ms(corr, steps, 1, stream)
+    ms_ls = _step_ms(lsum, steps, 1, stream)
+    torch.cuda.synchronize()
+    err = float((out - m.C).abs().max().item())
+    del That, out, Mhat, mk
+    torch.cuda.empty_cache()
+    return {"correlate_K_components_ms": ms_corr, "localsums_fp64_ms": ms_ls,
+            "what": "torch.fft (cuFFT): rfftn(g), K x (product, irfftn, times w); local sums FP64 rfftn/irfftn",
+            "max_abs_diff_vs_ttm_correlate": err}
+
+
+def forms_order4(ttm, ctx, wl, dev, steps, warmup, crop_voxels):
+    """FP32, FP16 and BF16 template spectra on the benchmark volume, each
+    timed (correlate + maximiser, double-float local sums) and checked
+    against the FP64 oracle at sampled valid voxels of the centred 128^3
+    crop. Both sides use a 24 x 64-rotation field (the per-tomogram kernels
+    do not depend on the quadrature)."""
+    import torch
+    import oracle as O
+    Z, Y, X = wl.tomo.shape
+    V = Z * Y * X
+    n, r = wl.order_n, wl.mask_radius
+    K = ttm.ttm_num_components(n)
+    p = ttm.params(order_n=n, mask_radius=r, n_rot_base=64)
+    t = torch.as_tensor(wl.template, device=dev)
+    field = torch.empty((K,) + wl.template.shape, dtype=torch.float64, device=dev)
+    ttm.ttm_build_tensor_field(ctx, t, p, field)
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    C = torch.empty((K, Z, Y, X), device=dev)
+    score = torch.empty((Z, Y, X), device=dev)
+    orient = torch.empty((3, Z, Y, X), device=dev)
+    vox = _crop_voxels((Z, Y, X), wl.template.shape, 128, crop_voxels, 11)
+    tv = torch.as_tensor(vox, device=dev)
+    pr = O.Prepared(wl.tomo, wl.template, r)
+    ofield = O.tensor_field(pr.tp, O.rotation_set(64), n, 3)
+    wref, _, _ = O.local_w(pr.g, pr.m, vox, False, pr.floor)
+    Cref = O.correlate(pr.g, ofield, vox, False, wref)
+    sref, _, _ = O.maximise(Cref, n, 3, 20000)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp32", ttm.TTM_PREC_FP32), ("fp16", ttm.TTM_PREC_FP16_SPECTRA),
+                       ("bf16", ttm.TTM_PREC_BF16_SPECTRA)):
+        plan = ttm.Plan(ctx, field, p, (Z, Y, X), precision=prec)
+        ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
+        mc = _step_ms(lambda: ttm.ttm_correlate(plan, d_tomo, C), steps, warmup, stream)
+        mp = _step_ms(lambda: ttm.ttm_peak_map(plan, C, score, orient), steps, warmup, stream)
+        got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
+        sg = score.flatten()[tv].cpu().numpy().astype(np.float64)
+        out[name] = {"correlate_ms": mc, "peak_map_ms": mp, "voxels_per_s": V / ((mc + mp) / 1e3),
+                     "C_max_abs_err": float(np.abs(got - Cref).max()),
+                     "C_rel_l2_err": float(np.linalg.norm(got - Cref) / np.linalg.norm(Cref)),
+                     "score_max_abs_err": float(np.abs(sg - sref).max())}
+        del plan
+    for name in ("fp16", "bf16"):
+        out[name]["vs_fp32_whole_step"] = out[name]["voxels_per_s"] / out["fp32"]["voxels_per_s"]
+        out[name]["vs_fp32_correlate"] = out["fp32"]["correlate_ms"] / out[name]["correlate_ms"]
+    out["error_sample"] = "%d valid voxels of the centred 128^3 crop vs the FP64 oracle" % vox.size
+    del C, score, orient, field
+    torch.cuda.empty_cache()
+    return out
+
+
+def plain_order6(ttm, ctx, dev, steps, warmup, crop_voxels):
+    """The plain FP32 form on the largest configuration: 1024 x 1024 x 256,
+    48^3 template, r = 19, n = 6 (28 components), 2000 copies at SNR 0.05;
+    timed per call, and checked against the FP64 oracle at sampled voxels of
+    the centred 128^3 crop (24 x 64-rotation field on both sides)."""
+    import torch
+    import oracle as O
+    t0 = time.perf_counter()
+    wl = synth.workload_order6()
+    gen_s = time.perf_counter() - t0
+    Z, Y, X = wl.tomo.shape
+    V = Z * Y * X
+    n, r = wl.order_n, wl.mask_radius
+    K = ttm.ttm_num_components(n)
+    p = ttm.params(order_n=n, mask_radius=r, n_rot_base=64)
+    t = torch.as_tensor(wl.template, device=dev)
+    field = torch.empty((K,) + wl.template.shape, dtype=torch.float64, device=dev)
+    ttm.ttm_build_tensor_field(ctx, t, p, field)
+    d_tomo = torch.as_tensor(wl.tomo, device=dev)
+    C = torch.empty((K, Z, Y, X), device=dev)
+    score = torch.empty((Z, Y, X), device=dev)
+    orient = torch.empty((3, Z, Y, X), device=dev)
+    plan = ttm.Plan(ctx, field, p, (Z, Y, X))
+    ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
+    stream = torch.cuda.current_stream()
+    mc = _step_ms(lambda: ttm.ttm_correlate(plan, d_tomo, C), steps, warmup, stream)
+    mp = _step_ms(lambda: ttm.ttm_peak_map(plan, C, score, orient), steps, warmup, stream)
+    vox = _crop_voxels((Z, Y, X), wl.template.shape, 128, crop_voxels, 13)
+    tv = torch.as_tensor(vox, device=dev)
+    got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
+    sg = score.flatten()[tv].cpu().numpy().astype(np.float64)
+    pr = O.Prepared(wl.tomo, wl.template, r)
+    ofield = O.tensor_field(pr.tp, O.rotation_set(64), n, 3)
+    wref, _, _ = O.local_w(pr.g, pr.m, vox, False, pr.floor)
+    Cref = O.correlate(pr.g, ofield, vox, False, wref)
+    sref, _, _ = O.maximise(Cref, n, 3, 20000)
+    del plan, C, score, orient, field, d_tomo
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "shape_zyx": [Z, Y, X], "order_n": n, "components": K,
+            "correlate_ms": mc, "peak_map_ms": mp, "voxels_per_s": V / ((mc + mp) / 1e3),
+            "local_sums": "double-float", "spectra": "fp32",
+            "C_max_abs_err": float(np.abs(got - Cref).max()), "score_max_abs_err": float(np.abs(sg - sref).max()),
+            "error_sample": "%d valid voxels of the centred 128^3 crop" % vox.size, "generation_s": gen_s}
+
+
 def run_ours(args, ws, rank, local):
     import torch
-    from paper_2408_02398_gb300 import build, synth
+    from paper_2408_02398_gb300 import build
     build.build()
     from paper_2408_02398_gb300 import ttm
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
     if args.zyx:
         # a smaller volume of the same workload (profiling captures): copies
         # scale with the volume
@@ -194,7 +454,8 @@ def run_ours(args, ws, rank, local):
     m = ttm.Matcher(ctx, wl.template, p, (Z, Y, X), device=dev)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    ttm.ttm_plan_set_localsum(m.plan, ttm.TTM_LOCALSUM_DF64 if args.localsum == "df64" else ttm.TTM_LOCALSUM_FP64)
+    ls_main = ttm.TTM_LOCALSUM_DF64 if args.localsum == "df64" else ttm.TTM_LOCALSUM_FP64
+    ttm.ttm_plan_set_localsum(m.plan, ls_main)
     d_tomo = torch.as_tensor(wl.tomo, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -212,12 +473,10 @@ def run_ours(args, ws, rank, local):
     launches0 = ttm.ttm_kernel_launches()
     barrier(ws)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0 = _events(stream)
     for _ in range(args.steps):
         step()
-    e1.record(stream)
+    e1 = _events(stream)
     torch.cuda.synchronize()
     barrier(ws)
     launches = ttm.ttm_kernel_launches() - launches0
@@ -229,71 +488,71 @@ def run_ours(args, ws, rank, local):
     ms_step = ms_total / args.steps
     value = V * args.steps * ws / (ms_total / 1e3)
 
-    # end to end through the public API with host buffers: pinned tomogram
-    # in, score + orientation maps out, copies inside the timed region
+    # the other local-sum arithmetic, same plan, same steps
+    other = ttm.TTM_LOCALSUM_FP64 if ls_main == ttm.TTM_LOCALSUM_DF64 else ttm.TTM_LOCALSUM_DF64
+    ttm.ttm_plan_set_localsum(m.plan, other)
+    ms_other = max_over_ranks(_step_ms(step, args.steps, 2, stream), ws, dev)
+    ttm.ttm_plan_set_localsum(m.plan, ls_main)
+
+    # end to end through the public calls with pinned host buffers
     h_tomo = torch.from_numpy(wl.tomo).pin_memory()
-    h_score = torch.empty((Z, Y, X), dtype=torch.float32).pin_memory()
-    h_orient = torch.empty((3, Z, Y, X), dtype=torch.float32).pin_memory()
-    d_in = torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+    ms_e2e = max_over_ranks(e2e_pipelined(ttm, m, h_tomo, args.steps, max(2, args.warmup // 2), dev), ws, dev)
+    e2e_value = V * ws / (ms_e2e / 1e3)
 
-    def e2e_step():
-        d_in.copy_(h_tomo, non_blocking=True)
-        ttm.ttm_correlate(m.plan, d_in, m.C)
-        ttm.ttm_peak_map(m.plan, m.C, m.score, m.orient, m.frob)
-        h_score.copy_(m.score, non_blocking=True)
-        h_orient.copy_(m.orient, non_blocking=True)
-
-    for _ in range(max(1, args.warmup // 2)):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier(ws)
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws, dev)
-    e2e_value = V * args.steps * ws / (ms_e2e / 1e3)
-
-    # Rooflines. Stages are per-step milliseconds of CUDA events on the
-    # launching stream. The dominant kernel is the maximiser (FP32-ALU
-    # bound): its algorithmic work is the dense probe contraction,
-    # 2 K P flops per voxel (P = 128 probe directions); the FP32 peak is
-    # 152 SMs x 128 lanes x 2 flops x the median SM clock sampled during the
-    # run. The correlate path (ttm_correlate) is HBM-bound: 4 + 4K bytes per
-    # voxel (read f, write K maps) against the measured copy bandwidth.
-    # `traffic` is dram read + write bytes per launch from one ncu capture
-    # of a 128 x 512 x 512 case, scaled by voxel count (traffic grows in
-    # proportion), for the kernels as they were when captured.
+    # Rooflines (stages: per-step milliseconds of CUDA events on the
+    # launching stream). The maximiser's dense work is the probe product on
+    # the tensor cores (FP16 mma.sync, same rate as BF16): 2 K_pad P flops
+    # per voxel (K padded to a multiple of 16, P = 128 probes), against the
+    # measured dense 16-bit peak; its time goes to the scalar Newton and
+    # start-selection work around that product (instruction issue), so the
+    # fraction is small by construction. The correlate path is HBM-bound:
+    # 4 + 4K algorithmic bytes per voxel (read f, write K maps).
     st_ms = {k: v / args.steps for k, v in stages.items()}
     corr_ms = sum(v for k, v in st_ms.items() if k != "peak_map")   # ttm_correlate
     pk, how = peaks_file()
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    probes = 128
-    pm_flops = 2.0 * K * probes * V
-    roof = {"bound": "alu", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
-            "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-            "peak_source": "FP32 FMA rate from unit counts at the sampled SM clock",
-            "traffic": 4.19e9, "flops_per_voxel": 2 * K * probes}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    tc_peak = float(pk.get("bf16_tflops", 1900.0))
+    kpad = (K + 15) // 16 * 16
+    pm_flops = 2.0 * kpad * 128 * V
+    roof_pm = {"bound": "tensor", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
+               "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+               "peak_source": how + " dense BF16 (burst); FP16 mma has the same rate",
+               "traffic": None, "flops_per_voxel": 2 * kpad * 128,
+               "note": "issue-bound on the scalar Newton / start work around the probe product"}
+    roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
     roof_corr = {"bound": "hbm", "kernel": "ttm_correlate (stages prefilter..xpass)",
                  "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                 "peak_source": how, "traffic": 28.1e9, "bytes_per_voxel": 4 + 4 * K}
+                 "peak_source": how, "traffic": None, "bytes_per_voxel": 4 + 4 * K}
     roof_corr["frac"] = roof_corr["achieved"] / roof_corr["peak"]
+    dominant = roof_pm if st_ms["peak_map"] >= corr_ms else roof_corr
+    other_roof = roof_corr if dominant is roof_pm else roof_pm
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, nv, dt, cores = oracle_sample_rate(wl, args.cpu_voxels)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d random valid-interior voxels (%.1f s): local normaliser, direct-sum correlation "
-                         "(15 components), 20000-sample + Newton maximiser; setup excluded" % (nv, dt)}
+    extras = {}
+    if rank == 0 and ws == 1 and not args.zyx:
+        if not args.no_comparators:
+            extras["comparators"] = {
+                "tm_per_rotation": tm_comparator(ttm, ctx, wl, p, dev, args.tm_rotations),
+                "cufft": cufft_comparator(ttm, m, wl, dev, max(2, args.steps // 2))}
+            tm = extras["comparators"]["tm_per_rotation"]
+            tm["ttm_speedup_vs_45123_rotations"] = tm["implied_45123_rotations_s"] * 1e3 / ms_step
+        if not args.no_forms:
+            del m
+            torch.cuda.empty_cache()
+            extras["forms"] = {"spectra_precision_order4": forms_order4(ttm, ctx, wl, dev, max(3, args.steps // 2),
+                                                                         2, args.crop_voxels),
+                               "plain_fp32_order6_1024x1024x256": plain_order6(ttm, ctx, dev, max(3, args.steps // 2),
+                                                                               2, args.crop_voxels)}
+        if not args.no_cpu:
+            rate, nv, dt, cores = oracle_sample_rate(wl, args.cpu_voxels)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d random valid-interior voxels (%.1f s): local normaliser, direct-sum correlation "
+                             "(15 components), 20000-sample + Newton maximiser; setup excluded" % (nv, dt)}
 
     if rank == 0:
+        names = {ttm.TTM_LOCALSUM_DF64: "double-float (FP32 pairs, ~48-bit significand)",
+                 ttm.TTM_LOCALSUM_FP64: "fp64"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -301,13 +560,16 @@ def run_ours(args, ws, rank, local):
                            "shape_zyx": [Z, Y, X], "template": 40, "order_n": n,
                            "components": K, "mask_radius": wl.mask_radius, "rotations_field": 24 * 2048,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1gpu",
-                           "local_sums": {"df64": "double-float (FP32 pairs, ~48-bit significand)",
-                                          "fp64": "fp64"}[args.localsum], "spectra": "fp32"},
-                "roofline": roof, "roofline_correlate": roof_corr, "stages_ms": st_ms, "setup_s": setup_s,
+                           "local_sums": names[ls_main], "spectra": "fp32", "sms": props.multi_processor_count},
+                "local_sums_other": {"local_sums": names[other], "value": V * ws / (ms_other / 1e3),
+                                     "ms_per_step": ms_other},
+                "roofline": dominant, "roofline_other": other_roof, "stages_ms": st_ms, "setup_s": setup_s,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": V * 4,
-                        "d2h_bytes_per_step": V * 4 * 4},
+                        "d2h_bytes_per_step": V * 4 * 4, "ms_per_step": ms_e2e,
+                        "how": "pinned host buffers, copy-in / compute / copy-out streams, two buffer sets"},
                 "gpu_launches": int(launches), "clocks": ck}
+        line.update(extras)
         print(json.dumps(line), flush=True)
 
 
@@ -851,6 +1113,29 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_qmap(args):
+    """A small case for kernel captures of the quaternion maximiser: a d' = 4
+    plan (n = 4, 16^3 template, r = 7, 24 x 64 field rotations) on a
+    --zyx white-noise tomogram (default 64 x 256 x 256); one correlation,
+    then --steps timed calls of the maximiser (CUDA events)."""
+    import torch
+    from paper_2408_02398_gb300 import build
+    build.build()
+    from paper_2408_02398_gb300 import ttm
+    shape = tuple(int(v) for v in (args.zyx or "64,256,256").split(","))
+    ctx = ttm.Context(0)
+    tmpl = synth.gaussian_blob_template(16, seed=5)
+    p = ttm.params(order_n=4, mask_radius=7.0, n_rot_base=64, dprime=4)
+    m = ttm.Matcher(ctx, tmpl, p, shape)
+    tomo = torch.as_tensor(synth.normals(3, 1, int(np.prod(shape))).reshape(shape).astype(np.float32), device="cuda")
+    m.run(tomo)
+    torch.cuda.synchronize()
+    ms = _step_ms(lambda: ttm.ttm_peak_map(m.plan, m.C, m.score, m.orient, m.frob), args.steps, 0,
+                  torch.cuda.current_stream())
+    print(json.dumps({"workload": "qmap", "shape_zyx": list(shape), "peak_map_ms": ms,
+                      "voxels_per_s": float(np.prod(shape)) / (ms / 1e3)}), flush=True)
+
+
 def next_smooth7(n):
     L = max(n, 2)
     while True:
@@ -871,9 +1156,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-voxels", type=int, default=250000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the forms block of the default line")
+    ap.add_argument("--no-comparators", action="store_true", help="skip the TM and cuFFT comparators")
+    ap.add_argument("--tm-rotations", type=int, default=256)
     ap.add_argument("--localsum", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the local sums of Eq. 2")
-    ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched", "quaternion", "blocked", "study"],
+    ap.add_argument("--workload", default="order4", choices=["order4", "mixed", "learned", "batched", "quaternion", "blocked", "study", "qmap"],
                     help="order4: the default plain FP32 workload; the others time one form against it")
     ap.add_argument("--zyx", default="", help="Z,Y,X of a smaller order-4 volume (profiling captures)")
     ap.add_argument("--crop-voxels", type=int, default=200)
@@ -895,6 +1183,8 @@ def main():
         run_blocked(args)
     elif args.workload == "study":
         run_study(args)
+    elif args.workload == "qmap":
+        run_qmap(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -291,16 +291,19 @@ ttm_status ttm_find_peaks(ttm_plan* plan, const float* d_map, int P, double min_
  * allocator (a framework's caching pool), or a streaming loop in which
  * cudaMalloc / cudaFree would synchronise the device and stall the work on
  * other streams.
- *   d_map    float32 [Z][Y][X] (device)
+ *   d_map    float32 [Z][Y][X] (device); every extent below 2^21
  *   box      host int[6]: z0, z1, y0, y1, x0, x1 (half-open), the search
  *            region (ttm_plan_valid_box gives the valid box of a plan)
  *   h_idx, h_val, h_count: as ttm_find_peaks (host; room for P entries)
  * Scratch is one fixed device array inside the library (about 3.3 MB per
  * device): at most 262144 local maxima in the box and P <= 16384. A larger
  * P, or a map with more local maxima in the box, fails with TTM_E_SHAPE
- * (nothing written to h_idx / h_val). The first call on a device does a
- * one-time set-up (it looks up the device address of that array with the
- * device current); make that first call before any stream capture begins.
+ * (nothing written to h_idx / h_val). The set-up is done by ttm_ctx_create:
+ * it looks up the device address of that array with the context's device
+ * current, which (under CUDA's lazy module loading) is also when the
+ * array's device memory is committed on that device; this call does no
+ * set-up of its own. The selection takes at most P passes over the
+ * surviving candidates on one SM (about 0.2 ms per pass over 262144).
  * Every call clears the array's candidate counter on `stream` before use.
  * All calls on one device share the array: calls that overlap (on other
  * streams or host threads) race and must be serialised by the caller.

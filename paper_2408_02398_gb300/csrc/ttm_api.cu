@@ -82,6 +82,7 @@ extern "C" ttm_status ttm_ctx_create(int device, ttm_ctx** out)
         TTM_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
         upload_probe_tables(c);
         upload_probe_tables4(c);
+        c->peak_scratch = peak_scratch_address();
         *out = c;
         return TTM_OK;
     } catch (const Error& e) {

@@ -93,6 +93,9 @@ void rotation_set(int64_t n_base, bool cube, std::vector<double>& q);
 void normalise_template_dev(ttm_ctx* ctx, const float* d_tmpl, int tz, int ty, int tx, const ttm_field_params& fp,
                             DevBuf& tp, cudaStream_t st);
 void exponents4(int n, std::vector<int>& e);
+// device address of the fixed scratch array of the allocation-free Find
+// Peaks on the current device (looked up once per context)
+void* peak_scratch_address();
 // probe tables of the quaternion maximiser, and the maximiser itself over
 // all V voxels (orient: [4][V] unit quaternions)
 void upload_probe_tables4(ttm_ctx* ctx);
@@ -127,6 +130,7 @@ struct ttm_ctx {
     size_t probe_half_off[3] = {0, 0, 0};
     ttm::DevBuf probe4;        // quaternion maximiser: probe quaternions and FP16 monomials
     size_t probe4_off[3] = {0, 0, 0};
+    void* peak_scratch = nullptr;  // device address of the allocation-free Find Peaks scratch
 };
 
 struct ttm_plan {

@@ -4,7 +4,6 @@
 // index) and compacts them; the host orders the candidates by (value desc,
 // index asc) and accepts greedily.
 #include <algorithm>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -150,24 +149,32 @@ static_assert(kOffCandVal % 256 == 0 && kOffOutIdx % 256 == 0 && kOffOutVal % 25
 
 static __device__ __align__(256) unsigned char g_peak_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_scratch_mu;
-static unsigned char* g_scratch_addr[kMaxDevices] = {};
-
-// One-time set-up per device, with that device current: the device address
-// of g_peak_scratch in this device's copy of the module.
-static unsigned char* static_scratch(int device)
+// Device address of g_peak_scratch in the current device's copy of the
+// module. Called once per context, at ttm_ctx_create, with the context's
+// device current: looking the symbol up loads the module on that device
+// (under lazy loading), which commits the array's device memory there and
+// then, not inside a later Find Peaks call.
+void* peak_scratch_address()
 {
-    TTM_REQUIRE(device >= 0 && device < kMaxDevices, E_UNSUPPORTED, "device ordinal beyond the static scratch table");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_peak_scratch);
-        if (e != cudaSuccess || !p)
-            throw Error{E_CUDA, std::string("cudaGetSymbolAddress(peak scratch): ") + cudaGetErrorString(e)};
-        g_scratch_addr[device] = static_cast<unsigned char*>(p);
-    }
-    return g_scratch_addr[device];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_peak_scratch);
+    if (e != cudaSuccess || !p)
+        throw Error{E_CUDA, std::string("cudaGetSymbolAddress(peak scratch): ") + cudaGetErrorString(e)};
+    return p;
+}
+
+// Candidates are kept as packed coordinates z << 42 | y << 21 | x (each
+// below 2^21), which order like the linear index (z, y, x lexicographic),
+// so the tie rule "lower index first" is unchanged and the distance test
+// needs shifts, not 64-bit divisions.
+__device__ __forceinline__ int64_t pack_zyx(int64_t i, int64_t X, int64_t Y)
+{
+    const int64_t x = i % X, r = i / X;
+    return ((r / Y) << 42) | ((r % Y) << 21) | x;
+}
+__device__ __forceinline__ int64_t unpack_index(int64_t c, int64_t X, int64_t Y)
+{
+    return ((c >> 42) * Y + ((c >> 21) & 0x1FFFFF)) * X + (c & 0x1FFFFF);
 }
 
 struct Best {
@@ -192,42 +199,81 @@ __device__ __forceinline__ Best shfl_best(const Best& b, int off)
     return o;
 }
 
-// Greedy selection over the compacted candidates (one CTA). Removed
-// candidates get index -1. *out_count = accepted peaks, or -1 when the
-// candidates overflowed the scratch.
+// Greedy selection over the compacted candidates (one CTA). The candidate
+// indices are first rewritten as packed coordinates; removed candidates
+// get -1. Every kCompactEvery accepted peaks the live candidates are
+// compacted in place (stable, one block-wide scan per 1024 entries), so
+// later passes only touch survivors. Cost: at most P passes over the live
+// candidates, each a few integer operations per candidate; at the caps
+// (262 144 candidates, P = 16 384) a pass over all of them is ~0.2 ms on one
+// SM, and compaction shrinks the live set as peaks suppress their
+// neighbourhoods. *out_count = accepted peaks, or -1 when the candidates
+// overflowed the scratch.
+constexpr int kCompactEvery = 8;
+
 __global__ void __launch_bounds__(1024) k_select_greedy(const unsigned long long* __restrict__ count, int64_t cap,
                                                         int P, double md2, int64_t X, int64_t Y,
-                                                        int64_t* __restrict__ cidx, const float* __restrict__ cval,
+                                                        int64_t* __restrict__ cidx, float* __restrict__ cval,
                                                         int64_t* __restrict__ oidx, float* __restrict__ oval,
                                                         int* __restrict__ out_count)
 {
     __shared__ Best warp_best[32];
     __shared__ Best chosen;
+    __shared__ int warp_live[32];
     const unsigned long long nn = *count;
     if (nn > (unsigned long long)cap) {
         if (threadIdx.x == 0) *out_count = -1;
         return;
     }
-    const int64_t n = (int64_t)nn;
+    int64_t n = (int64_t)nn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) cidx[k] = pack_zyx(cidx[k], X, Y);
+    __syncthreads();
     bool have = false;
-    double az = 0, ay = 0, ax = 0;
+    int64_t az = 0, ay = 0, ax = 0;
     int got = 0;
     for (int it = 0; it < P; it++) {
+        if (it > 0 && it % kCompactEvery == 0) {
+            // stable in-place compaction of the live candidates
+            int64_t base = 0;
+            for (int64_t k0 = 0; k0 < n; k0 += blockDim.x) {
+                const int64_t k = k0 + threadIdx.x;
+                const int64_t c = k < n ? cidx[k] : -1;
+                const float v = k < n ? cval[k] : 0.f;
+                const bool live = c >= 0;
+                const unsigned ball = __ballot_sync(0xffffffffu, live);
+                if (lane == 0) warp_live[warp] = __popc(ball);
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int wi = 0; wi < nwarps; wi++) {
+                    if (wi < warp) before += warp_live[wi];
+                    total += warp_live[wi];
+                }
+                before += __popc(ball & ((1u << lane) - 1u));
+                __syncthreads();  // every read of this chunk precedes its writes
+                if (live) {
+                    cidx[base + before] = c;
+                    cval[base + before] = v;
+                }
+                base += total;
+                __syncthreads();
+            }
+            n = base;
+        }
         Best b{0.f, 0, -1};
         for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-            const int64_t i = cidx[k];
-            if (i < 0) continue;
+            const int64_t c = cidx[k];
+            if (c < 0) continue;
             if (have) {
-                const double x = (double)(i % X), y = (double)((i / X) % Y), z = (double)(i / (X * Y));
-                const double dz = z - az, dy = y - ay, dx = x - ax;
+                const double dz = (double)((c >> 42) - az), dy = (double)(((c >> 21) & 0x1FFFFF) - ay),
+                             dx = (double)((c & 0x1FFFFF) - ax);
                 if (dz * dz + dy * dy + dx * dx < md2) {
                     cidx[k] = -1;
                     continue;
                 }
             }
-            const Best c{cval[k], i, k};
-            if (better(c, b)) b = c;
+            const Best cb{cval[k], c, k};
+            if (better(cb, b)) b = cb;
         }
         for (int off = 16; off > 0; off >>= 1) {
             const Best o = shfl_best(b, off);
@@ -244,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_select_greedy(const unsigned long long
             if (lane == 0) {
                 chosen = b;
                 if (b.pos >= 0) {
-                    oidx[it] = b.i;
+                    oidx[it] = unpack_index(b.i, X, Y);
                     oval[it] = b.v;
                     cidx[b.pos] = -1;
                 }
@@ -255,9 +301,9 @@ __global__ void __launch_bounds__(1024) k_select_greedy(const unsigned long long
         if (c.pos < 0) break;
         got++;
         have = true;
-        ax = (double)(c.i % X);
-        ay = (double)((c.i / X) % Y);
-        az = (double)(c.i / (X * Y));
+        az = c.i >> 42;
+        ay = (c.i >> 21) & 0x1FFFFF;
+        ax = c.i & 0x1FFFFF;
         __syncthreads();
     }
     if (threadIdx.x == 0) *out_count = got;
@@ -277,10 +323,12 @@ extern "C" ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, i
                         box[3] <= Y && box[4] >= 0 && box[4] <= box[5] && box[5] <= X,
                     E_INVALID_ARG, "box must satisfy 0 <= lo <= hi <= extent on every axis");
         TTM_REQUIRE(P <= kStaticPeaks, E_SHAPE, "P exceeds the static peak capacity of 16384");
+        TTM_REQUIRE(Z < (1 << 21) && Y < (1 << 21) && X < (1 << 21), E_SHAPE, "extents must be below 2^21");
         *h_count = 0;
         if (P == 0) return TTM_OK;
         TTM_CUDA_TRY(cudaSetDevice(ctx->device));
-        unsigned char* s = static_scratch(ctx->device);
+        TTM_REQUIRE(ctx->peak_scratch, E_INTERNAL, "context has no peak scratch address");
+        unsigned char* s = static_cast<unsigned char*>(ctx->peak_scratch);
         cudaStream_t st = (cudaStream_t)stream;
         int64_t* cidx = reinterpret_cast<int64_t*>(s + kOffCandIdx);
         float* cval = reinterpret_cast<float*>(s + kOffCandVal);

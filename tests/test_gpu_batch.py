@@ -51,8 +51,9 @@ def gpu_field(T, ctx, tmpl, p):
     return f
 
 
-def run_plan(T, ctx, field, p, tomo, work_shape=None):
+def run_plan(T, ctx, field, p, tomo, work_shape=None, localsum=0):
     plan = T.Plan(ctx, field, p, tomo.shape, work_shape=work_shape)
+    T.ttm_plan_set_localsum(plan, localsum)
     K = field.shape[0]
     Zw, Yw, Xw = plan.shape
     d_C = torch.empty((K, Zw, Yw, Xw), device="cuda")
@@ -212,3 +213,40 @@ def test_batch_vs_oracle(T, ctx, batch_setup):
         sref, _, _ = O.maximise(Cref, n, 3, nsamples=20000)
         z, y, x = np.unravel_index(vox, shape)
         assert np.abs(sc.cpu().numpy()[z, y, x] - sref).max() <= S_TOL
+
+
+def test_batch_double_float_localsums(T, ctx, batch_setup):
+    """TTM_BATCH_LOCALSUM_DF64: the batch with double-float local sums equals
+    per-pair plans set to TTM_LOCALSUM_DF64 bit for bit, and its scores
+    match the FP64 oracle at sampled valid voxels within the FP32 score
+    tolerance."""
+    p, tmpls, fields, tomos, _, _ = batch_setup
+    r, n = 5.0, 4
+    items = []
+    for i, s in enumerate(SHAPES):
+        for j in range(2):
+            items.append((i, j, torch.full(s, -7.0, device="cuda"), torch.zeros((3,) + s, device="cuda"),
+                          torch.zeros(s, device="cuda")))
+    B = T.Batch(ctx, p, fields, tomos, items, n_branches=2, flags=T.TTM_BATCH_LOCALSUM_DF64)
+    B.run()
+    torch.cuda.synchronize()
+    ofield = {}
+    for i, j, sc, ori, fr in items:
+        plan, d_C, d_s, d_u, d_F = run_plan(T, ctx, fields[j], p, tomos[i].cpu().numpy(),
+                                            work_shape=B.work_shape(i), localsum=1)
+        bs = box_slice(plan.valid_box())
+        assert torch.equal(sc[bs], d_s[bs])
+        assert torch.equal(ori[(slice(None),) + bs], d_u[(slice(None),) + bs])
+        shape = SHAPES[i]
+        tomo = tomos[i].cpu().numpy().astype(np.float64)
+        pr = O.Prepared(tomo, tmpls[j].astype(np.float64), r)
+        if j not in ofield:
+            ofield[j] = O.tensor_field(pr.tp, O.rotation_set(16), n, 3)
+        vox = O.valid_voxels(shape, tmpls[j].shape)
+        vox = np.sort(np.random.default_rng(7 + i + 10 * j).choice(vox, 300, replace=False))
+        w, _, _ = O.local_w(pr.g, pr.m, vox, periodic=False, floor=pr.floor)
+        Cref = O.correlate(pr.g, ofield[j], vox, periodic=False, w=w)
+        sref, _, _ = O.maximise(Cref, n, 3, nsamples=20000)
+        z, y, x = np.unravel_index(vox, shape)
+        assert np.abs(sc.cpu().numpy()[z, y, x] - sref).max() <= S_TOL
+        assert np.abs(d_C.cpu().numpy()[:, z, y, x] - Cref).max() <= C_TOL * max(1.0, np.abs(Cref).max())

@@ -5,7 +5,11 @@ that span several tiles and leave ragged tails.
 Tolerances: C maps max abs error <= 2e-5 (FP32 FFT correlation of values
 |C| <= 1), w relative 1e-5, score abs error <= 1e-4 (FP32), orientation <=
 1 degree where the maximum is well separated (best minus second-best
-distinct local maximum > 1e-3 |s|), peak lists bit-exact."""
+distinct local maximum > 1e-3 |s|), peak lists bit-exact.
+
+The local sums of Eq. 2 have two arithmetics on the GPU, FP64 and
+double-float (pairs of FP32 numbers, ~48-bit significand); every test of the
+correlation runs both (LOCALSUMS) against the same FP64 oracle values."""
 import math
 
 import numpy as np
@@ -19,7 +23,10 @@ pytestmark = pytest.mark.gpu
 
 C_TOL = 2e-5
 S_TOL = 1e-4
+W_TOL = 1e-5
 ANG_TOL_DEG = 1.0
+# TTM_LOCALSUM_FP64, TTM_LOCALSUM_DF64
+LOCALSUMS = [0, 1]
 
 
 @pytest.fixture(scope="module")
@@ -87,8 +94,9 @@ CASES = [
 ]
 
 
-def run_gpu(T, ctx, tomo, field, p):
+def run_gpu(T, ctx, tomo, field, p, localsum=0):
     plan = T.Plan(ctx, dev(field, torch.float64), p, tomo.shape)
+    T.ttm_plan_set_localsum(plan, localsum)
     K = field.shape[0]
     d_C = torch.empty((K,) + tomo.shape, dtype=torch.float32, device="cuda")
     T.ttm_correlate(plan, dev(tomo), d_C)
@@ -102,19 +110,20 @@ def run_gpu(T, ctx, tomo, field, p):
     return plan, d_C, d_w, d_s, d_u, d_F
 
 
+@pytest.mark.parametrize("localsum", LOCALSUMS)
 @pytest.mark.parametrize("shape,N,r,n", CASES)
-def test_correlate_periodic_all_voxels(T, ctx, shape, N, r, n):
+def test_correlate_periodic_all_voxels(T, ctx, shape, N, r, n, localsum):
     """C and w on the whole grid against the oracle's periodic direct sums."""
     tomo = synth.normals(7 + N, 1, int(np.prod(shape))).reshape(shape).astype(np.float32)
     tmpl = synth.gaussian_blob_template(N, seed=N)
     field = oracle_field(tmpl, r, n, 16)
     p = T.params(order_n=n, mask_radius=r, n_rot_base=16)
-    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p, localsum)
     pr = O.Prepared(tomo.astype(np.float64), tmpl, r)
     w, _, _ = O.local_w(pr.g, pr.m, None, periodic=True, floor=pr.floor)
     Cref = O.correlate(pr.g, field, None, periodic=True, w=w)
     got_w = d_w.cpu().numpy().ravel()
-    assert np.abs(got_w - w).max() <= 1e-5 * np.abs(w).max()
+    assert np.abs(got_w - w).max() <= W_TOL * np.abs(w).max()
     got = d_C.cpu().numpy().reshape(field.shape[0], -1)
     assert np.abs(got - Cref).max() <= C_TOL * max(1.0, np.abs(Cref).max())
     # Frobenius proxy
@@ -130,21 +139,22 @@ REG_CASES = [
 ]
 
 
+@pytest.mark.parametrize("localsum", LOCALSUMS)
 @pytest.mark.parametrize("shape,N,r,n", REG_CASES)
-def test_correlate_register_lengths(T, ctx, shape, N, r, n):
+def test_correlate_register_lengths(T, ctx, shape, N, r, n, localsum):
     """C, w, score at sampled voxels (periodic) for the register FFT lengths."""
     V = int(np.prod(shape))
     tomo = synth.normals(11 + N, 1, V).reshape(shape).astype(np.float32)
     tmpl = synth.gaussian_blob_template(N, seed=N + 1)
     field = oracle_field(tmpl, r, n, 16)
     p = T.params(order_n=n, mask_radius=r, n_rot_base=16)
-    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p, localsum)
     rng = np.random.default_rng(N)
     vox = np.sort(rng.choice(V, size=1500, replace=False))
     pr = O.Prepared(tomo.astype(np.float64), tmpl, r)
     w, _, _ = O.local_w(pr.g, pr.m, vox, periodic=True, floor=pr.floor)
     Cref = O.correlate(pr.g, field, vox, periodic=True, w=w)
-    assert np.abs(d_w.cpu().numpy().ravel()[vox] - w).max() <= 1e-5 * np.abs(w).max()
+    assert np.abs(d_w.cpu().numpy().ravel()[vox] - w).max() <= W_TOL * np.abs(w).max()
     K = field.shape[0]
     got = d_C.cpu().numpy().reshape(K, -1)[:, vox]
     assert np.abs(got - Cref).max() <= C_TOL * max(1.0, np.abs(Cref).max())
@@ -182,7 +192,8 @@ def test_peak_map_random_tensors(T, ctx, n):
     assert np.abs(d_F.cpu().numpy().ravel() - 1.0).max() < 1e-5
 
 
-def test_degenerate_inputs(T, ctx):
+@pytest.mark.parametrize("localsum", LOCALSUMS)
+def test_degenerate_inputs(T, ctx, localsum):
     """Constant tomogram: where the mask ball stays clear of the zero-padded
     outer layer the local variance is zero -> w = 0 -> C = 0, score 0;
     next to the outer layer w follows the oracle."""
@@ -191,7 +202,7 @@ def test_degenerate_inputs(T, ctx):
     field = oracle_field(tmpl, 3.0, 2, 4)
     p = T.params(order_n=2, mask_radius=3.0, n_rot_base=4)
     tomo = np.full(shape, 2.5, np.float32)
-    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p, localsum)
     z0, z1, y0, y1, x0, x1 = plan.valid_box()
     inner = (slice(z0 + 1, z1 - 1), slice(y0 + 1, y1 - 1), slice(x0 + 1, x1 - 1))
     assert np.all(d_w.cpu().numpy()[inner] == 0)
@@ -333,54 +344,98 @@ def test_small_workload_maps(T, small):
             assert angle_deg(gu[i], res["orient"][i]) <= ANG_TOL_DEG
 
 
+def peak_groups(ov, tol):
+    """Runs of consecutive peaks whose values lie within tol of the next one:
+    inside a run the order may legitimately differ between two maps that
+    agree to tol/2."""
+    out, j = [], 0
+    while j < len(ov):
+        k = j
+        while k + 1 < len(ov) and ov[k] - ov[k + 1] <= tol:
+            k += 1
+        out.append((j, k + 1))
+        j = k + 1
+    return out
+
+
 def test_small_workload_peaks(T, small):
-    """Top peaks of the GPU score and Frobenius maps equal the oracle's
-    wherever the ranking is not decided by less than the score tolerance."""
+    """Peak lists of the GPU score and Frobenius maps against the oracle's
+    (16 peaks asked, the first 12 compared). Every peak whose value is more
+    than 2 * S_TOL from its neighbours sits at the same rank with the same
+    index; a run of peaks closer than that must hold the same set of
+    indices. Every oracle peak within 4 voxels of a planted centre is
+    among the compared ones and is matched that way."""
     wl, m, res = small
     Z, Y, X = wl.tomo.shape
     box = m.plan.valid_box()
+    cen = np.asarray(wl.planted.centres, dtype=float)
     for key, gmap in (("score", m.score), ("F", m.frob)):
         full = np.full(Z * Y * X, -np.inf)
         full[res["vox"]] = res[key]
-        oi, ov = O.find_peaks(full.reshape(Z, Y, X), box, 12, 2 * wl.mask_radius)
-        gi, gv = T.ttm_find_peaks(m.plan, gmap, 12, 2 * wl.mask_radius)
-        # compare the prefix of peaks separated from their successors by > 2 tol
-        k = len(ov)
-        for j in range(len(ov) - 1):
-            if ov[j] - ov[j + 1] <= 2 * S_TOL:
-                k = j
-                break
-        assert k >= 3
-        assert np.array_equal(gi[:k], oi[:k]), (key, gi[:k], oi[:k])
+        oi, ov = O.find_peaks(full.reshape(Z, Y, X), box, 16, 2 * wl.mask_radius)
+        gi, gv = T.ttm_find_peaks(m.plan, gmap, 16, 2 * wl.mask_radius)
+        assert len(gi) == len(oi) == 16
+        compared = 0
+        for j, k in peak_groups(ov, 2 * S_TOL):
+            if j >= 12 or k == len(ov):
+                break   # a run cut by the list end may continue past it
+            assert set(gi[j:k]) == set(oi[j:k]), (key, j, gi[j:k], oi[j:k])
+            compared = k
+        assert compared >= 10, (key, compared)
+        pos = {int(i): v for i, v in zip(gi, gv)}
+        for i, v in zip(oi[:compared], ov[:compared]):
+            assert abs(pos[int(i)] - v) <= S_TOL
+        zyx = np.stack([oi // (Y * X), (oi // X) % Y, oi % X], axis=1).astype(float)
+        near = np.min(np.linalg.norm(zyx[:, None, :] - cen[None, :, :], axis=2), axis=1) <= 4.0
+        assert near[:compared].sum() >= 2 and near[compared:12].sum() == 0, (key, near)
 
 
 # ---------------------------------------------- full size, bench config --
 
-def test_fullsize_order4_sampled(T, ctx):
+@pytest.fixture(scope="module")
+def fullsize(T, ctx):
     """512 x 512 x 200 low-passed noise, 40^3 template, r = 16, n = 4, 300
-    planted copies: the exact shapes and launch configuration the benchmark
-    times, checked at sampled valid-interior voxels (including every fifth
-    planted centre) against the oracle computed voxel by voxel. The
-    quadrature is reduced to 24 x 64 rotations on both sides (the
-    per-tomogram kernels do not depend on it)."""
+    planted copies: the shapes and launch configuration the benchmark
+    times. The oracle is evaluated voxel by voxel at 10 000 random valid
+    voxels plus every planted centre. The quadrature is reduced to 24 x 64
+    rotations on both sides (the per-tomogram kernels do not depend on it)."""
     wl = synth.workload_order4()
     n, r = wl.order_n, wl.mask_radius
     p = T.params(order_n=n, mask_radius=r, n_rot_base=64)
     m = T.Matcher(ctx, wl.template, p, wl.tomo.shape)
-    m.run(dev(wl.tomo))
-    torch.cuda.synchronize()
     Z, Y, X = wl.tomo.shape
     valid = O.valid_voxels(wl.tomo.shape, wl.template.shape)
     rng = np.random.default_rng(3)
-    cent = np.array([(c[0] * Y + c[1]) * X + c[2] for c in wl.planted.centres[::5]], dtype=np.int64)
-    vox = np.unique(np.concatenate([valid[rng.choice(valid.size, 60, replace=False)], cent]))
+    cent = np.array([(c[0] * Y + c[1]) * X + c[2] for c in wl.planted.centres], dtype=np.int64)
+    vox = np.unique(np.concatenate([valid[rng.choice(valid.size, 10000, replace=False)], cent]))
     res = O.ttm(wl.tomo, wl.template, r, n, O.rotation_set(64), vox)
+    return wl, m, vox, cent, res
+
+
+@pytest.mark.parametrize("localsum", LOCALSUMS)
+def test_fullsize_order4_sampled(T, fullsize, localsum):
+    """The benchmark's workload in both local-sum arithmetics: field, w, C,
+    score and (where well defined) orientation at >= 10 000 sampled voxels
+    and at all 300 planted centres."""
+    wl, m, vox, cent, res = fullsize
+    T.ttm_plan_set_localsum(m.plan, localsum)
+    m.run(dev(wl.tomo))
+    d_w = torch.empty(wl.tomo.shape, dtype=torch.float32, device="cuda")
+    T.ttm_plan_copy_w(m.plan, d_w)
+    torch.cuda.synchronize()
+    assert vox.size >= 10000 and np.isin(cent, vox).all()
     assert np.abs(m.field.cpu().numpy() - res["T"]).max() <= 1e-12 * np.abs(res["T"]).max()
+    gw = d_w.cpu().numpy().ravel()[vox]
+    assert np.abs(gw - res["w"]).max() <= W_TOL * np.abs(res["w"]).max()
     K = res["C"].shape[0]
     gC = m.C.cpu().numpy().reshape(K, -1)[:, vox]
     assert np.abs(gC - res["C"]).max() <= C_TOL
     gs = m.score.cpu().numpy().ravel()[vox]
-    assert np.abs(gs - res["score"]).max() <= S_TOL
+    err = np.abs(gs - res["score"])
+    assert err.max() <= S_TOL, (err.max(), int((err > S_TOL).sum()))
+    gF = m.frob.cpu().numpy().ravel()[vox]
+    assert np.abs(gF - res["F"]).max() <= 3 * C_TOL
     gu = m.orient.cpu().numpy().reshape(3, -1)[:, vox].T
     ok = well_defined(res)
+    assert ok.mean() > 0.5
     assert angle_deg(gu[ok], res["orient"][ok]).max() <= ANG_TOL_DEG

@@ -312,6 +312,58 @@ def test_local_w_linear_ramp_closed_form():
     assert np.all(wc == 0)
 
 
+def test_local_w_zero_variance_floor_counts_sliver_windows():
+    """The zero-variance floor of the normaliser (w = 0 where the local
+    variance is at most 1e-8 M mean(g^2)), on windows that hold only a
+    sliver of an object in an exactly empty background.
+
+    Volume: zeros, a block of ones far away (it sets mean(g^2)) and a single
+    voxel of value v at c0. The mask is the radius-1 ball (centre and its 6
+    face neighbours, M = 7). After the 3-tap filter (0.2, 0.6, 0.2 per axis)
+    the single voxel becomes a 3x3x3 cube of products of taps: 0.216 v at
+    c0, 0.072 v on faces, 0.024 v on edges, 0.008 v on corners. By hand:
+      - windows that touch that cube are the cube dilated by the 6-neighbour
+        ball: 27 + 6 * 9 = 81 voxels;
+      - the window at c0 sees 0.216 v and six 0.072 v: S1 = 0.648 v,
+        S2 = 0.07776 v^2, var = S2 - S1^2 / 7 = 0.0177737... v^2 (the
+        largest of the 81);
+      - the window at c0 + (2, 1, 1) sees one corner only: var = 0.008^2
+        (1 - 1/7) v^2 = 5.4857e-5 v^2 (the smallest, 324 times less).
+    v is chosen so that the largest sliver variance is 1e-9 M mean(g^2):
+    all 81 lie between the two floors, so exactly 81 voxels have w = 0 at
+    1e-8 but w > 0 at 1e-12 (block-interior and empty windows have zero
+    variance, block-edge windows variance far above both floors)."""
+    Z = Y = X = 26
+    f = np.zeros((Z, Y, X))
+    f[15:23, 15:23, 15:23] = 1.0
+    m, M = O.mask((3, 3, 3), 1.0)
+    assert M == 7
+    c0 = (6, 7, 8)
+    g_block = O.filter3(f)
+    E_block = M * float(np.mean(g_block ** 2))
+    var_max_unit = 0.07776 - 0.648 ** 2 / 7.0
+    v = math.sqrt(1e-9 * E_block / var_max_unit)
+    f[c0] = v
+    g = O.filter3(f)
+    E = M * float(np.mean(g ** 2))
+    vox = O.valid_voxels(g.shape, m.shape)
+    w8, _, _ = O.local_w(g, m, vox, floor=1e-8 * E)
+    w12, _, _ = O.local_w(g, m, vox, floor=1e-12 * E)
+    wd, _, _ = O.local_w(g, m, vox)          # the default floor is the 1e-8 one
+    assert np.array_equal(wd, w8)
+    sliver = (w8 == 0) & (w12 > 0)
+    assert int(sliver.sum()) == 81
+    zz, yy, xx = np.unravel_index(vox[sliver], g.shape)
+    d = np.abs(np.stack([zz, yy, xx], 1) - np.array(c0))
+    # inside the dilated cube: at most 2 per axis and at most one axis at 2
+    assert np.all(d.max(1) <= 2) and np.all((d == 2).sum(1) <= 1)
+    at = {tuple(p): k for k, p in enumerate(np.stack([zz, yy, xx], 1))}
+    k_c = at[c0]
+    k_corner = at[(c0[0] + 2, c0[1] + 1, c0[2] + 1)]
+    assert w12[sliver][k_c] == pytest.approx(1.0 / math.sqrt(var_max_unit * v * v), rel=1e-9)
+    assert w12[sliver][k_corner] == pytest.approx(1.0 / math.sqrt(0.008 ** 2 * (6.0 / 7.0) * v * v), rel=1e-9)
+
+
 def test_local_w_periodic_agrees_in_interior():
     g = synth.normals(9, 1, 20 ** 3).reshape(20, 20, 20)
     m, _ = O.mask((7, 7, 7), 3.0)
@@ -391,6 +443,72 @@ def test_tm_recovers_planted_quarter_turn():
     best, idx = O.tm(g, tp, quats, v, w=w)
     assert idx[0] == 1
     assert best[0] == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.slow
+def test_brute_force_tm_agrees_with_ttm_ref_on_planted_copies():
+    """Classical TM at fine angular sampling (Eqs. 1, 6, 7 over 100 008
+    super-Fibonacci rotations, cube-symmetrised) against TTM on a tiny
+    volume: a 20 x 20 x 22 tomogram with two copies of a compact 9^3
+    four-Gaussian template, planted at rotations taken from the TM list
+    (so TM's answer at the copies is defined: that index), light white
+    noise (sigma 0.02). Over the whole valid interior:
+      - TM's two highest peaks (exclusion 2 r) are the planted centres, and
+        its best rotation there is the planted one;
+      - TTM's score peaks (d' = 4, n = 4, Sec. 3.1) lie within r_s = 3
+        voxels of them (Sec. 3.3: TTM peaks may be shifted);
+      - TTM-ref (Alg. 3, r_s = 3) moves them exactly onto TM's peaks, with
+        rotations within 3 degrees of TM's.
+    The d' = 3 axis u* against TM's best R e_z is printed, not gated."""
+    N, r = 9, 4.0
+    tmpl = synth.gaussian_blob_template(N, seed=7, n_blobs=4, centre_radius=2.5, std_lo=0.7, std_hi=1.6)
+    shape = (20, 20, 22)
+    Q = O.rotation_set(4167, cube=True)
+    assert Q.shape[0] >= 100000
+    planted_idx = [31337, 77777]
+    cen = np.array([[7, 7, 7], [13, 12, 14]])
+    vol = np.zeros(shape)
+    synth.plant(vol, tmpl, cen, Q[planted_idx], 1.0)
+    vol += 0.02 * synth.normals(98, 1, vol.size).reshape(shape)
+    pr = O.Prepared(vol, tmpl, r)
+    vox = O.valid_voxels(shape, tmpl.shape)
+    Z, Y, X = shape
+    box = (N // 2, Z - (N - N // 2) + 1, N // 2, Y - (N - N // 2) + 1, N // 2, X - (N - N // 2) + 1)
+    w, _, _ = O.local_w(pr.g, pr.m, vox, False, pr.floor)
+    best, bidx = O.tm(pr.g, pr.tp, Q, vox, False, w)
+    full = np.full(Z * Y * X, -np.inf)
+    full[vox] = best
+    tm_pk, tm_val = O.find_peaks(full.reshape(shape), box, 2, 2 * r)
+    cen_idx = (cen[:, 0] * Y + cen[:, 1]) * X + cen[:, 2]
+    assert set(tm_pk.tolist()) == set(cen_idx.tolist())
+    pos = {int(v): k for k, v in enumerate(vox)}
+    for c, qi in zip(cen_idx, planted_idx):
+        assert bidx[pos[int(c)]] == qi
+    # TTM, the paper's quaternion form
+    F4 = O.tensor_field(pr.tp, O.rotation_set(512), 4, 4)
+    C = O.correlate(pr.g, F4, vox, False, w)
+    s4, _, _ = O.maximise(C, 4, 4, 20000)
+    full = np.full(Z * Y * X, -np.inf)
+    full[vox] = s4
+    ttm_pk, _ = O.find_peaks(full.reshape(shape), box, 2, 2 * r)
+
+    def zyx(i):
+        return np.array([i // (Y * X), (i // X) % Y, i % X], dtype=float)
+    for c in cen_idx:
+        assert min(np.linalg.norm(zyx(c) - zyx(p)) for p in ttm_pk) <= 3.0
+    ref_pk, ref_q, _, _ = O.ttm_refine(pr, F4, 4, ttm_pk, 3.0)
+    assert set(ref_pk.tolist()) == set(tm_pk.tolist())
+    for p, q in zip(ref_pk, ref_q):
+        q_tm = Q[bidx[pos[int(p)]]]
+        assert math.degrees(2 * math.acos(min(1.0, abs(float(np.dot(q, q_tm)))))) <= 3.0
+    # reported: the d' = 3 needle axis against TM's best R e_z
+    F3 = O.tensor_field(pr.tp, O.rotation_set(512), 4, 3)
+    for c in cen_idx:
+        k = pos[int(c)]
+        _, u3, _ = O.maximise(O.correlate(pr.g, F3, vox[k:k + 1], False, w[k:k + 1]), 4, 3, 20000)
+        ez = O.quat_to_rot(Q[bidx[k]])[:, 2]
+        print("d'=3 u* vs TM R e_z at %s: %.1f deg" % (tuple(int(t) for t in zyx(c)),
+                                                     math.degrees(math.acos(min(1.0, abs(float(u3[0] @ ez)))))))
 
 
 # ------------------------------------------------------------- maximiser --
