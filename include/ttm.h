@@ -69,9 +69,9 @@ typedef struct ttm_mlp ttm_mlp;
  *                    over unit directions u in S^2 (K = binom(n+2,2));
  *                    4: the quaternion powers q^{(x)n} of Sec. 3, maximised
  *                    over unit quaternions (K = binom(n+3,3): 10, 35, 84):
- *                    a full rotation, roll included. Field and correlation
- *                    are built for n = 2, 4, 6, the maximiser for n = 2, 4;
- *                    the learned maximiser and the batch are d' = 3 only
+ *                    a full rotation, roll included. Field, correlation
+ *                    and maximiser are built for n = 2, 4, 6; the learned
+ *                    maximiser and the batch are d' = 3 only
  *   mask_radius      r of the spherical mask m (Sec. 2, after Eq. 3), voxels
  *   mask_soft_width  width of the raised-cosine edge beyond r; 0 = binary
  *   filter_a         a of the filter h with z-transform 1 + a(z + 1/z - 2)

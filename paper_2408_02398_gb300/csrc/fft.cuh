@@ -82,6 +82,18 @@ template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1
     a3 = csub(t1, t3);
 }
 
+// x * (h + DIR h i) = h (x.x - DIR x.y) + i h (x.y + DIR x.x): two adds and
+// two products instead of a full complex product
+template <int DIR, typename R> __device__ __forceinline__ cx<R> mul_w8_1(cx<R> x, R h)
+{
+    return DIR < 0 ? mk<R>((x.x + x.y) * h, (x.y - x.x) * h) : mk<R>((x.x - x.y) * h, (x.y + x.x) * h);
+}
+// x * (-h + DIR h i) = h (-x.x - DIR x.y) + i h (DIR x.x - x.y)
+template <int DIR, typename R> __device__ __forceinline__ cx<R> mul_w8_3(cx<R> x, R h)
+{
+    return DIR < 0 ? mk<R>((x.y - x.x) * h, (-x.x - x.y) * h) : mk<R>((-x.x - x.y) * h, (x.x - x.y) * h);
+}
+
 template <int DIR, typename R> __device__ __forceinline__ void dft8(cx<R>* v)
 {
     cx<R> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
@@ -90,63 +102,91 @@ template <int DIR, typename R> __device__ __forceinline__ void dft8(cx<R>* v)
     dft4<DIR>(o0, o1, o2, o3);
     const R h = (R)OddRadixConst::sqrt_half;
     // w8^1 = h(1 + DIR i), w8^2 = DIR i, w8^3 = h(-1 + DIR i)
-    cx<R> t1 = cmul(o1, mk<R>(h, (R)DIR * h));
+    cx<R> t1 = mul_w8_1<DIR, R>(o1, h);
     cx<R> t2 = cmul_diri<DIR>(o2);
-    cx<R> t3 = cmul(o3, mk<R>(-h, (R)DIR * h));
+    cx<R> t3 = mul_w8_3<DIR, R>(o3, h);
     v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
     v[1] = cadd(e1, t1); v[5] = csub(e1, t1);
     v[2] = cadd(e2, t2); v[6] = csub(e2, t2);
     v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
 }
 
-// odd radix R: y_k = a_0 + sum_{r=1}^{(R-1)/2} [(a_r + a_{R-r}) cos(2 pi rk/R)
-//                      + DIR i (a_r - a_{R-r}) sin(2 pi rk/R)]
-template <int RAD, int DIR, typename R> __device__ __forceinline__ void dft_odd(cx<R>* v)
+// Odd radices in their symmetric form: with t_r = x_r + x_{R-r} and
+// d_r = x_r - x_{R-r} (r = 1..(R-1)/2),
+//   X_0 = x_0 + sum_r t_r,
+//   X_k, X_{R-k} = A_k +- DIR i B_k,  A_k = x_0 + sum_r t_r cos(2 pi rk/R),
+//                                      B_k = sum_r d_r sin(2 pi rk/R),
+// so every product is a real constant times a complex value and each
+// cosine / sine term is shared by the output pair (k, R - k).
+template <int DIR, typename R> __device__ __forceinline__ cx<R> pm_diri(cx<R> a, cx<R> b, bool plus)
 {
-    constexpr int H = (RAD - 1) / 2;
-    R cs[RAD], sn[RAD];
-    cs[0] = 1; sn[0] = 0;
-    if (RAD == 3) { cs[1] = (R)OddRadixConst::c3; sn[1] = (R)OddRadixConst::s3; }
-    if (RAD == 5) {
-        cs[1] = (R)OddRadixConst::c5_1; sn[1] = (R)OddRadixConst::s5_1;
-        cs[2] = (R)OddRadixConst::c5_2; sn[2] = (R)OddRadixConst::s5_2;
-    }
-    if (RAD == 7) {
-        cs[1] = (R)OddRadixConst::c7_1; sn[1] = (R)OddRadixConst::s7_1;
-        cs[2] = (R)OddRadixConst::c7_2; sn[2] = (R)OddRadixConst::s7_2;
-        cs[3] = (R)OddRadixConst::c7_3; sn[3] = (R)OddRadixConst::s7_3;
-    }
-#pragma unroll
-    for (int m = H + 1; m < RAD; m++) { cs[m] = cs[RAD - m]; sn[m] = -sn[RAD - m]; }
-    cx<R> sp[H + 1], dm[H + 1];
-#pragma unroll
-    for (int r = 1; r <= H; r++) { sp[r] = cadd(v[r], v[RAD - r]); dm[r] = csub(v[r], v[RAD - r]); }
-    cx<R> out[RAD];
-#pragma unroll
-    for (int k = 0; k < RAD; k++) {
-        cx<R> acc = v[0];
-        cx<R> is = mk<R>(0, 0);
-#pragma unroll
-        for (int r = 1; r <= H; r++) {
-            int m = (r * k) % RAD;
-            acc.x += sp[r].x * cs[m];
-            acc.y += sp[r].y * cs[m];
-            is.x += dm[r].x * sn[m];
-            is.y += dm[r].y * sn[m];
-        }
-        // + DIR i * is
-        out[k] = cadd(acc, cmul_diri<DIR>(is));
-    }
-#pragma unroll
-    for (int k = 0; k < RAD; k++) v[k] = out[k];
+    // a + DIR i b (plus) or a - DIR i b
+    const cx<R> ib = cmul_diri<DIR>(b);
+    return plus ? cadd(a, ib) : csub(a, ib);
+}
+
+template <int DIR, typename R> __device__ __forceinline__ void dft3(cx<R>* v)
+{
+    const cx<R> t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const cx<R> x0 = v[0];
+    v[0] = cadd(x0, t);
+    const cx<R> A = csub(x0, cscale(t, (R)0.5));
+    const cx<R> B = cscale(d, (R)OddRadixConst::s3);
+    v[1] = pm_diri<DIR, R>(A, B, true);
+    v[2] = pm_diri<DIR, R>(A, B, false);
+}
+
+template <int DIR, typename R> __device__ __forceinline__ void dft5(cx<R>* v)
+{
+    const R c1 = (R)OddRadixConst::c5_1, c2 = (R)OddRadixConst::c5_2;
+    const R s1 = (R)OddRadixConst::s5_1, s2 = (R)OddRadixConst::s5_2;
+    const cx<R> x0 = v[0];
+    const cx<R> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const cx<R> d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+    v[0] = cadd(x0, cadd(t1, t2));
+    // cos 4 pi/5 = c2, cos 8 pi/5 = c1; sin 8 pi/5 = -s1
+    const cx<R> A1 = cadd(x0, cadd(cscale(t1, c1), cscale(t2, c2)));
+    const cx<R> A2 = cadd(x0, cadd(cscale(t1, c2), cscale(t2, c1)));
+    const cx<R> B1 = cadd(cscale(d1, s1), cscale(d2, s2));
+    const cx<R> B2 = csub(cscale(d1, s2), cscale(d2, s1));
+    v[1] = pm_diri<DIR, R>(A1, B1, true);
+    v[4] = pm_diri<DIR, R>(A1, B1, false);
+    v[2] = pm_diri<DIR, R>(A2, B2, true);
+    v[3] = pm_diri<DIR, R>(A2, B2, false);
+}
+
+template <int DIR, typename R> __device__ __forceinline__ void dft7(cx<R>* v)
+{
+    const R c1 = (R)OddRadixConst::c7_1, c2 = (R)OddRadixConst::c7_2, c3 = (R)OddRadixConst::c7_3;
+    const R s1 = (R)OddRadixConst::s7_1, s2 = (R)OddRadixConst::s7_2, s3 = (R)OddRadixConst::s7_3;
+    const cx<R> x0 = v[0];
+    const cx<R> t1 = cadd(v[1], v[6]), t2 = cadd(v[2], v[5]), t3 = cadd(v[3], v[4]);
+    const cx<R> d1 = csub(v[1], v[6]), d2 = csub(v[2], v[5]), d3 = csub(v[3], v[4]);
+    v[0] = cadd(x0, cadd(t1, cadd(t2, t3)));
+    // angles 2 pi rk / 7 reduced: (r k mod 7) in {1,2,3} keeps its sine, in
+    // {4,5,6} takes minus the sine of 7 - (r k mod 7)
+    const cx<R> A1 = cadd(x0, cadd(cscale(t1, c1), cadd(cscale(t2, c2), cscale(t3, c3))));
+    const cx<R> A2 = cadd(x0, cadd(cscale(t1, c2), cadd(cscale(t2, c3), cscale(t3, c1))));
+    const cx<R> A3 = cadd(x0, cadd(cscale(t1, c3), cadd(cscale(t2, c1), cscale(t3, c2))));
+    const cx<R> B1 = cadd(cscale(d1, s1), cadd(cscale(d2, s2), cscale(d3, s3)));
+    const cx<R> B2 = csub(cscale(d1, s2), cadd(cscale(d2, s3), cscale(d3, s1)));
+    const cx<R> B3 = cadd(csub(cscale(d1, s3), cscale(d2, s1)), cscale(d3, s2));
+    v[1] = pm_diri<DIR, R>(A1, B1, true);
+    v[6] = pm_diri<DIR, R>(A1, B1, false);
+    v[2] = pm_diri<DIR, R>(A2, B2, true);
+    v[5] = pm_diri<DIR, R>(A2, B2, false);
+    v[3] = pm_diri<DIR, R>(A3, B3, true);
+    v[4] = pm_diri<DIR, R>(A3, B3, false);
 }
 
 template <int RAD, int DIR, typename R> __device__ __forceinline__ void dft(cx<R>* v)
 {
     if constexpr (RAD == 2) dft2<DIR>(v);
+    else if constexpr (RAD == 3) dft3<DIR, R>(v);
     else if constexpr (RAD == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
-    else if constexpr (RAD == 8) dft8<DIR, R>(v);
-    else dft_odd<RAD, DIR, R>(v);
+    else if constexpr (RAD == 5) dft5<DIR, R>(v);
+    else if constexpr (RAD == 7) dft7<DIR, R>(v);
+    else dft8<DIR, R>(v);
 }
 
 // ----------------------------------------------------------- stages --

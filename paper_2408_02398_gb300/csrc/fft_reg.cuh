@@ -135,8 +135,7 @@ k_fs_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro pro
     __syncthreads();
     fs_phase1<R, E, P, DIR>(x, p, xa + w * S::LD, tw);
     __syncthreads();
-#pragma unroll
-    for (int ii = 0; ii < E / P; ii++) {
+    auto column = [&](int ii) {
         const int k1 = p + P * ii;
         cx<R> u[P];
 #pragma unroll
@@ -146,6 +145,15 @@ k_fs_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro pro
 #pragma unroll
             for (int k2 = 0; k2 < P; k2++) store(u[k2], o, i, k1 + E * k2);
         }
+    };
+    if constexpr (sizeof(R) >= 8) {
+        // FP64 / double-float butterflies are long: one copy of the
+        // P-point DFT keeps the kernel inside the instruction cache
+#pragma unroll 1
+        for (int ii = 0; ii < E / P; ii++) column(ii);
+    } else {
+#pragma unroll
+        for (int ii = 0; ii < E / P; ii++) column(ii);
     }
 }
 
@@ -172,8 +180,7 @@ k_fs_contig(const cx<R>* __restrict__ in, int64_t nlines, const void* twg, Pro p
     __syncthreads();
     fs_phase1<R, E, P, DIR>(x, p, xa + w * S::LD, tw);
     __syncthreads();
-#pragma unroll
-    for (int ii = 0; ii < E / P; ii++) {
+    auto column = [&](int ii) {
         const int k1 = p + P * ii;
         cx<R> u[P];
 #pragma unroll
@@ -183,6 +190,13 @@ k_fs_contig(const cx<R>* __restrict__ in, int64_t nlines, const void* twg, Pro p
 #pragma unroll
             for (int k2 = 0; k2 < P; k2++) store(u[k2], l, 0, k1 + E * k2);
         }
+    };
+    if constexpr (sizeof(R) >= 8) {
+#pragma unroll 1
+        for (int ii = 0; ii < E / P; ii++) column(ii);
+    } else {
+#pragma unroll
+        for (int ii = 0; ii < E / P; ii++) column(ii);
     }
 }
 

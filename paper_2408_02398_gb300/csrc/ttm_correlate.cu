@@ -106,8 +106,10 @@ struct SinkNormalise {
     {
         int64_t i = row * X + x;
         // w is read-only for the whole pass: the read-only path lets these
-        // loads be issued ahead of the stores to C
-        C[(int64_t)batch * V + i] = __ldg(w + i) * v;
+        // loads be issued ahead of the stores to C. C is written once and
+        // read back only by the maximiser: streaming (evict-first) stores
+        // keep it from displacing what the passes reuse in L2.
+        __stcs(C + (int64_t)batch * V + i, __ldg(w + i) * v);
     }
 };
 
@@ -172,7 +174,7 @@ struct SinkNormaliseScaled {
     {
         int64_t i = row * X + x;
         const float g = __ldg(gmax);
-        C[(int64_t)batch * V + i] = __ldg(w + i) * v * (__ldg(fac + batch) * (g > 0.f ? g : 1.f));
+        __stcs(C + (int64_t)batch * V + i, __ldg(w + i) * v * (__ldg(fac + batch) * (g > 0.f ? g : 1.f)));
     }
 };
 
@@ -342,7 +344,7 @@ void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st
                  (const float*)nullptr, 1.f, st);
     stage_end(P, ST_ZCORR, st);
     launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
-                              StoreTo<float>{work, ncols, Xh}, st);
+                                  StoreTo<float>{work, ncols, Xh}, st);
     stage_end(P, ST_YPASS, st);
     launch_c2r_any<float>(work, (int64_t)Z * Y, SinkNormalise{d_C, p.w.as<float>(), V, X}, p.px32, P->K, st);
     stage_end(P, ST_XPASS, st);
@@ -404,7 +406,8 @@ extern "C" ttm_status ttm_plan_create_padded(ttm_ctx* ctx, const double* d_field
 
         plan_build_spectra(P, d_field);
         const int64_t Vh = (int64_t)Z * Y * P->prep.Xh;
-        P->work.alloc(P->K * Vh * (precision == TTM_PREC_FP32 ? sizeof(float2) : sizeof(__half2)));
+        const size_t elem = precision == TTM_PREC_FP32 ? sizeof(float2) : sizeof(__half2);
+        P->work.alloc(P->K * Vh * elem);
         const int64_t V = (int64_t)Z * Y * X;
         P->cand_cap = V / 8 + 64;  // strict 26-neighbour maxima are >= 2 apart per axis
         P->cand.alloc(P->cand_cap * (sizeof(int64_t) + sizeof(float)));

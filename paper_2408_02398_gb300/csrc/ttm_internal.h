@@ -129,7 +129,7 @@ struct ttm_ctx {
     ttm::DevBuf probe_half;    // FP16 monomial tables for the tensor-core probe product
     size_t probe_half_off[3] = {0, 0, 0};
     ttm::DevBuf probe4;        // quaternion maximiser: probe quaternions and FP16 monomials
-    size_t probe4_off[3] = {0, 0, 0};
+    size_t probe4_off[4] = {0, 0, 0, 0};
     void* peak_scratch = nullptr;  // device address of the allocation-free Find Peaks scratch
 };
 

@@ -1015,8 +1015,6 @@ extern "C" ttm_status ttm_peak_map(ttm_plan* plan, const float* d_C, ttm_maximis
         TTM_REQUIRE(mode == TTM_MAX_PLAIN || mlp != nullptr, E_INVALID_ARG, "the learned maximiser needs an mlp");
         TTM_REQUIRE(plan->fp.dprime == 3 || mode == TTM_MAX_PLAIN, E_UNSUPPORTED,
                     "the learned maximiser works on the 2-sphere (d' = 3)");
-        TTM_REQUIRE(plan->fp.dprime == 3 || plan->fp.order_n <= 4, E_UNSUPPORTED,
-                    "the quaternion maximiser is built for n = 2 and 4");
         TTM_CUDA_TRY(cudaSetDevice(plan->ctx->device));
         const Prep& p = plan->prep;
         const int64_t V = (int64_t)p.Z * p.Y * p.X;

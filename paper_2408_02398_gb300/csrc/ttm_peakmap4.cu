@@ -20,8 +20,11 @@
 //    bits), in shared memory [cell][thread];
 //  * starts by angular suppression over the cell bests: the best probe,
 //    then the best cell best farther than 25 degrees (|q . q_s| <
-//    cos 25 deg) from every start taken, if within 0.2 ||C||_F of the best,
-//    up to 4 starts (2 for n = 2);
+//    cos 25 deg) from every start taken, if within 0.2 ||C||_F (n = 4) or
+//    0.5 ||C||_F (n = 6) of the best, up to 4 (n = 4) or 6 (n = 6) starts;
+//  * n = 2 needs no probes: p = q^T A q with A_ij = C_{e_i + e_j}, whose
+//    maximum over unit q is the top eigenpair of the symmetric 4 x 4
+//    matrix A (cyclic Jacobi rotations), polished by Newton;
 //  * up to three Riemannian Newton steps from every start in turn (one copy
 //    of the step code, so the kernel stays small in the instruction cache),
 //    then up to twelve on the best. S^3 is parallelisable: q (x) i,
@@ -54,11 +57,16 @@ constexpr int kP4Cells = kP4 / 8;        // one cell per 8-column MMA tile
 constexpr int kP4Threads = 256;
 constexpr int kP4Pre = 3;                // Newton steps per start (starts in turn)
 constexpr int kP4Polish = 12;            // Newton steps on the best start
-constexpr float kP4Margin = 0.2f;        // starts within this * ||C||_F of the best
 constexpr float kP4SepCos = 0.90630779f; // starts lie farther apart than 25 degrees
 
 __host__ __device__ constexpr int ncomp4(int n) { return (n + 1) * (n + 2) * (n + 3) / 6; }
-__host__ __device__ constexpr int nstarts4(int n) { return n >= 4 ? 4 : 2; }
+// Starts within this * ||C||_F of the best probe. The drop of the form from
+// a maximum to the nearest probe is at most half the Hessian bound
+// n (n - 1) ||C||_F times the squared probe spacing, so the margin scales
+// with n (n - 1): 0.2 at n = 4 (chosen by emulation against the oracle),
+// 0.5 at n = 6.
+__host__ __device__ constexpr float p4_margin(int n) { return n >= 6 ? 0.5f : 0.2f; }
+__host__ __device__ constexpr int nstarts4(int n) { return n >= 6 ? 6 : (n >= 4 ? 4 : 2); }
 __host__ __device__ constexpr int p4_kx(int n) { return (ncomp4(n) + 15) / 16 * 16; }
 __host__ __device__ constexpr int p4_kxs(int n) { return p4_kx(n) + 8; }
 __host__ __device__ constexpr int p4_kp(int n) { return (ncomp4(n) + 3) / 4 * 4; }
@@ -303,7 +311,74 @@ struct Probe4Tables {
     const float4* dir;    // [kP4] (w, x, y, z), rows as p4_row
     const __half* phi2h;  // [kP4][p4_kxs(2)] FP16 weighted monomials
     const __half* phi4h;  // [kP4][p4_kxs(4)]
+    const __half* phi6h;  // [kP4][p4_kxs(6)]
 };
+
+// Top eigenpair of the symmetric 4 x 4 matrix A (00 01 02 03 11 12 13 22
+// 23 33) by cyclic Jacobi rotations (each zeroes one off-diagonal entry;
+// 6 sweeps leave the off-diagonal part at FP32 rounding). Returns the
+// largest eigenvalue and its unit eigenvector in q.
+__device__ __forceinline__ float top_eig4(const float* A, float* q)
+{
+    float a[4][4], v[4][4];
+    {
+        int ij = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = i; j < 4; j++, ij++) { a[i][j] = A[ij]; a[j][i] = A[ij]; }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[i][j] = i == j ? 1.f : 0.f;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 6; sweep++) {
+#pragma unroll
+        for (int p = 0; p < 3; p++)
+#pragma unroll
+            for (int r = p + 1; r < 4; r++) {
+                const float apr = a[p][r];
+                if (apr == 0.f) continue;
+                // rotation angle: tan(2 theta) = 2 a_pr / (a_rr - a_pp)
+                const float th = (a[r][r] - a[p][p]) / (2.f * apr);
+                const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+                const float c = rsqrtf(t * t + 1.f), sn = t * c;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {  // columns p, r
+                    const float akp = a[k][p], akr = a[k][r];
+                    a[k][p] = c * akp - sn * akr;
+                    a[k][r] = sn * akp + c * akr;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {  // rows p, r
+                    const float apk = a[p][k], ark = a[r][k];
+                    a[p][k] = c * apk - sn * ark;
+                    a[r][k] = sn * apk + c * ark;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float vkp = v[k][p], vkr = v[k][r];
+                    v[k][p] = c * vkp - sn * vkr;
+                    v[k][r] = sn * vkp + c * vkr;
+                }
+            }
+    }
+    int b = 0;
+#pragma unroll
+    for (int i = 1; i < 4; i++)
+        if (a[i][i] > a[b][b]) b = i;
+    float lam = a[0][0];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (i == b) lam = a[i][i];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (i == b) q[k] = v[k][i];
+    }
+    normalise4(q);
+    return lam;
+}
 
 // shared memory: one region of 32-bit words [row][kXStride], column =
 // thread, that holds first the staged FP16 input ([KX / 2] rows of half
@@ -325,7 +400,7 @@ __host__ __device__ constexpr size_t p4_smem_bytes()
 }
 
 template <int N>
-__global__ void __launch_bounds__(kP4Threads, 2)
+__global__ void __launch_bounds__(kP4Threads, N >= 6 ? 1 : 2)
 k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
            float* __restrict__ frob, Probe4Tables tabs)
 {
@@ -342,7 +417,7 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
     // FP16 copies of the directions, only for the 25-degree separation tests
     uint2* sdirh = reinterpret_cast<uint2*>(phih + kP4 * KXS);
     {
-        const uint4* src = reinterpret_cast<const uint4*>(N == 2 ? tabs.phi2h : tabs.phi4h);
+        const uint4* src = reinterpret_cast<const uint4*>(N == 2 ? tabs.phi2h : (N == 4 ? tabs.phi4h : tabs.phi6h));
         uint4* dst = reinterpret_cast<uint4*>(phih);
         for (int i = threadIdx.x; i < kP4 * KXS / 8; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < kP4; i += blockDim.x) {
@@ -377,6 +452,19 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             for (int k2 = K; k2 < KP; k2++) c[k2] = 0.f;
         }
         const float F = sqrtf(F2);
+        float bp = 0.f, bq[4] = {1.f, 0.f, 0.f, 0.f};
+        if constexpr (N == 2) {
+            if (F > 0.f) {
+                float A[10];
+#pragma unroll
+                for (int i = 0; i < 10; i++) A[i] = c[i];  // C . q^0: the matrix itself
+                top_eig4(A, bq);
+                bp = form4<N>(c, bq, A);
+#pragma unroll 1
+                for (int it = 0; it < kP4Polish; it++)
+                    if (newton_step4<N>(c, F, bq, bp, A, 4)) break;
+            }
+        } else {
         // Probe product on the tensor cores: x = C / ||C||_F is staged in
         // FP16 in this thread's column of the key region (rows = component
         // pairs) and loaded as the A fragments of both 16-voxel tiles of the
@@ -462,7 +550,7 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             }
             int last = p4_row(bc, best & 7u);
             rows = (uint64_t)last;
-            const uint32_t thr = hkey(hkey_value(best) - kP4Margin, 0u);
+            const uint32_t thr = hkey(hkey_value(best) - p4_margin(N), 0u);
             uint64_t alive = 0ull;
             uint32_t bk = 0u;
             int bcell = -1;
@@ -505,7 +593,6 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             }
         }
         __syncwarp();  // the key rows are restaged by the next voxel block
-        float bp = 0.f, bq[4] = {1.f, 0.f, 0.f, 0.f};
         if (F > 0.f) {
             float bA[10];
             bp = -INFINITY;
@@ -529,6 +616,7 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             for (int it = 0; it < kP4Polish; it++)
                 if (newton_step4<N>(c, F, bq, bp, bA, 4)) break;
         }
+        }  // N > 2
         // canonical sign: the first non-zero of (w, x, y, z) positive
         const bool neg = bq[0] < 0.f ||
                          (bq[0] == 0.f && (bq[1] < 0.f || (bq[1] == 0.f && (bq[2] < 0.f || (bq[2] == 0.f && bq[3] < 0.f)))));
@@ -552,8 +640,8 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
 // cell is the lowest-index unassigned probe and its 7 nearest unassigned
 // neighbours (distance |q . q'|, as q ~ -q), member m of cell c placed at
 // table row p4_row(c, m). Layout: directions [kP4] float4, then the FP32
-// weighted monomials mult(alpha) q^alpha for n = 2 and 4, [kP4][p4_kp(n)].
-static void build_probe4(std::vector<float>& out, size_t off[3])
+// weighted monomials mult(alpha) q^alpha for n = 2, 4 and 6, [kP4][p4_kp(n)].
+static void build_probe4(std::vector<float>& out, size_t off[4])
 {
     std::vector<double> q;
     rotation_set(kP4, false, q);
@@ -586,7 +674,7 @@ static void build_probe4(std::vector<float>& out, size_t off[3])
     for (int j : src)
         for (int k = 0; k < 4; k++) out.push_back((float)q[4 * j + k]);
     int slot = 1;
-    for (int n : {2, 4}) {
+    for (int n : {2, 4, 6}) {
         off[slot++] = out.size();
         std::vector<int> e;
         exponents4(n, e);
@@ -616,14 +704,15 @@ __global__ void k_phi4_half(const float* __restrict__ phi, int KP, int K, int KX
 void upload_probe_tables4(ttm_ctx* ctx)
 {
     std::vector<float> h;
-    size_t off[3];
+    size_t off[4];
     build_probe4(h, off);
     DevBuf f32;
     f32.alloc(h.size() * sizeof(float));
     TTM_CUDA_TRY(cudaMemcpy(f32.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
     const size_t dir_bytes = sizeof(float4) * kP4;
     const size_t h2 = sizeof(__half) * (size_t)kP4 * p4_kxs(2), h4 = sizeof(__half) * (size_t)kP4 * p4_kxs(4);
-    ctx->probe4.alloc(dir_bytes + h2 + h4);
+    const size_t h6 = sizeof(__half) * (size_t)kP4 * p4_kxs(6);
+    ctx->probe4.alloc(dir_bytes + h2 + h4 + h6);
     TTM_CUDA_TRY(cudaMemcpy(ctx->probe4.p, f32.p, dir_bytes, cudaMemcpyDeviceToDevice));
     unsigned char* base = ctx->probe4.as<unsigned char>();
     k_phi4_half<<<64, 256>>>(f32.as<float>() + off[1], p4_kp(2), ncomp4(2), p4_kxs(2),
@@ -632,10 +721,14 @@ void upload_probe_tables4(ttm_ctx* ctx)
     k_phi4_half<<<64, 256>>>(f32.as<float>() + off[2], p4_kp(4), ncomp4(4), p4_kxs(4),
                              reinterpret_cast<__half*>(base + dir_bytes + h2));
     TTM_LAUNCH_CHECK();
+    k_phi4_half<<<64, 256>>>(f32.as<float>() + off[3], p4_kp(6), ncomp4(6), p4_kxs(6),
+                             reinterpret_cast<__half*>(base + dir_bytes + h2 + h4));
+    TTM_LAUNCH_CHECK();
     TTM_CUDA_TRY(cudaDeviceSynchronize());
     ctx->probe4_off[0] = 0;
     ctx->probe4_off[1] = dir_bytes;
     ctx->probe4_off[2] = dir_bytes + h2;
+    ctx->probe4_off[3] = dir_bytes + h2 + h4;
 }
 
 void peakmap4_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, float* orient, float* frob,
@@ -644,9 +737,11 @@ void peakmap4_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, 
     const unsigned char* base = ctx->probe4.as<unsigned char>();
     const Probe4Tables t{reinterpret_cast<const float4*>(base + ctx->probe4_off[0]),
                          reinterpret_cast<const __half*>(base + ctx->probe4_off[1]),
-                         reinterpret_cast<const __half*>(base + ctx->probe4_off[2])};
+                         reinterpret_cast<const __half*>(base + ctx->probe4_off[2]),
+                         reinterpret_cast<const __half*>(base + ctx->probe4_off[3])};
     const int64_t blocks = std::max<int64_t>(1, ceil_div(V, kP4Threads));
-    // two resident CTAs per SM; a grid stride balances the uneven Newton work
+    // two resident CTAs per SM (one at n = 6); a grid stride balances the
+    // uneven Newton work
     const int64_t grid = std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 16);
 #define TTM_P4_LAUNCH(N_)                                                                                       \
     {                                                                                                            \
@@ -657,7 +752,8 @@ void peakmap4_run(ttm_ctx* ctx, int n, const float* C, int64_t V, float* score, 
     switch (n) {
         case 2: TTM_P4_LAUNCH(2); break;
         case 4: TTM_P4_LAUNCH(4); break;
-        default: throw Error{E_UNSUPPORTED, "the quaternion maximiser is built for n = 2 and 4"};
+        case 6: TTM_P4_LAUNCH(6); break;
+        default: throw Error{E_UNSUPPORTED, "the quaternion maximiser is built for n = 2, 4 and 6"};
     }
 #undef TTM_P4_LAUNCH
     TTM_LAUNCH_CHECK();

@@ -234,6 +234,59 @@ struct StoreWDF {
     }
 };
 
+// Fused z pass of the local sums: per tile of W adjacent (y, x) columns,
+// the forward transform along z, the product with the (real, even) mask
+// spectrum and the inverse transform, through shared memory (Stockham
+// stages: one copy of each butterfly, which keeps the long FP64 /
+// double-float kernels inside the instruction cache). One read and one
+// write of the (g, g^2) spectrum instead of two each.
+template <typename R, class Mask>
+__global__ void __launch_bounds__(256)
+k_zmask(cx<R>* __restrict__ zd, int64_t ncols, LenPlan pl, int W, int ld, Mask mask)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* bufb = bufa + W * ld;
+    cx<R>* tws = bufb + W * ld;
+    const int Z = pl.L;
+    const int64_t c0 = (int64_t)blockIdx.x * W;
+    load_twiddles<R>(tws, pl);
+    for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+        const int z = idx / W, w = idx - z * W;
+        const int64_t c = c0 + w;
+        bufa[w * ld + z] = c < ncols ? zd[(int64_t)z * ncols + c] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    cx<R>* p = smem_fft<-1, R>(bufa, bufb, ld, W, pl, tws);
+    cx<R>* q = (p == bufa) ? bufb : bufa;
+    for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+        const int kz = idx / W, w = idx - kz * W;
+        const int64_t c = c0 + w;
+        if (c < ncols) p[w * ld + kz] = mask(p[w * ld + kz], 0, c, kz);
+    }
+    __syncthreads();
+    cx<R>* r = smem_fft<+1, R>(p, q, ld, W, pl, tws);
+    for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
+        const int z = idx / W, w = idx - z * W;
+        const int64_t c = c0 + w;
+        if (c < ncols) zd[(int64_t)z * ncols + c] = r[w * ld + z];
+    }
+}
+
+template <typename R, class Mask>
+static void launch_zmask(cx<R>* zd, int64_t ncols, const LenPlan& pz, Mask mask, cudaStream_t st)
+{
+    const int Z = pz.L;
+    const int ld = Z | 1;
+    int W = 16;
+    while (W > 2 && (2 * (size_t)W * ld + Z) * sizeof(cx<R>) > 110 * 1024) W /= 2;
+    const size_t smem = (2 * (size_t)W * ld + Z) * sizeof(cx<R>);
+    auto k = k_zmask<R, Mask>;
+    set_smem(k, smem);
+    k<<<(unsigned)ceil_div(ncols, W), 256, smem, st>>>(zd, ncols, pz, W, ld, mask);
+    TTM_LAUNCH_CHECK();
+}
+
 __global__ void k_octant_to_df(const double* __restrict__ in, int64_t n, float2* __restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -327,8 +380,9 @@ void prep_spectrum(Prep& p, cudaStream_t st)
                               ProIdentity<float>(), StoreTo<float>{G, 0, (int64_t)Y * Xh}, st);
 }
 
-// local sums: forward x, y, z of (g + i g^2), times the mask spectrum,
-// inverse z, y, x with the w epilogue; in FP64 or in double-float
+// local sums: forward x, y of (g + i g^2), the fused z pass (forward,
+// times the mask spectrum, inverse), inverse y, x with the w epilogue; in
+// FP64 or in double-float
 void prep_localsums(Prep& p, cudaStream_t st)
 {
     const int Z = p.Z, Y = p.Y, X = p.X;
@@ -338,10 +392,7 @@ void prep_localsums(Prep& p, cudaStream_t st)
         launch_contig_any<df64, -1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(), StoreTo<df64>{zd, X, 1}, st);
         launch_strided_any<df64, -1>(zd, StridedAxis{X, Z, YX, X}, p.pyd, ProIdentity<df64>(),
                                      StoreTo<df64>{zd, YX, X}, st);
-        launch_strided_any<df64, -1>(zd, StridedAxis{YX, 1, 0, YX}, p.pzd, ProIdentity<df64>(),
-                                     StoreTo<df64>{zd, 0, YX}, st);
-        launch_strided_any<df64, +1>(zd, StridedAxis{YX, 1, 0, YX}, p.pzd,
-                                     ProMaskSpectrumDF{p.mhat_df.as<float2>(), Z, Y, X}, StoreTo<df64>{zd, 0, YX}, st);
+        launch_zmask<df64>(zd, YX, p.pzd, ProMaskSpectrumDF{p.mhat_df.as<float2>(), Z, Y, X}, st);
         launch_strided_any<df64, +1>(zd, StridedAxis{X, Z, YX, X}, p.pyd, ProIdentity<df64>(),
                                      StoreTo<df64>{zd, YX, X}, st);
         launch_contig_any<df64, +1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(),
@@ -352,10 +403,7 @@ void prep_localsums(Prep& p, cudaStream_t st)
     launch_contig_any<double, -1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(), StoreTo<double>{zc, X, 1}, st);
     launch_strided_any<double, -1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
                                    StoreTo<double>{zc, YX, X}, st);
-    launch_strided_any<double, -1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64, ProIdentity<double>(),
-                                   StoreTo<double>{zc, 0, YX}, st);
-    launch_strided_any<double, +1>(zc, StridedAxis{YX, 1, 0, YX}, p.pz64,
-                                   ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, StoreTo<double>{zc, 0, YX}, st);
+    launch_zmask<double>(zc, YX, p.pz64, ProMaskSpectrum{p.mhat.as<double>(), Z, Y, X}, st);
     launch_strided_any<double, +1>(zc, StridedAxis{X, Z, YX, X}, p.py64, ProIdentity<double>(),
                                    StoreTo<double>{zc, YX, X}, st);
     launch_contig_any<double, +1>(zc, (int64_t)Z * Y, p.px64, ProIdentity<double>(),
