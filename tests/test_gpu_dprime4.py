@@ -278,3 +278,41 @@ def test_ttm_refine_matches_oracle(T, ctx):
     with pytest.raises(T.TTMError) as e:
         T.ttm_refine_peaks(m3.plan, dev(tmpl), m.orient, starts[:1], 3.0)
     assert e.value.code == 3
+
+
+# ------------------------------------------------ synthetic accuracy study --
+
+def test_study_noise_free_copies_recovered_exactly(T, ctx):
+    """The synthetic accuracy study (the analogue of Sec. 5.1, run in full by
+    bench.py --workload study), reduced to one cell: 27 copies of the 21^3
+    six-Gaussian template on a 3 x 3 x 3 grid at uniform random rotations,
+    noise-free, the quaternion form at n = 4 (24 x 2048 field rotations).
+    The 27 highest Frobenius peaks at exclusion 2r (Sec. 3.2, 3.4) lie
+    within 3 voxels of the copies (the shift Sec. 3.3 describes), and
+    TTM-ref (Alg. 3, r_s = 3) puts every copy on its exact centre with the
+    planted rotation to within 1 degree."""
+    N, r, n = 21, 9.0, 4
+    tmpl = synth.gaussian_blob_template(N, seed=11).astype(np.float32)
+    vol, pl = synth.grid_tomogram(tmpl, 3, 26, 4, 31, None, r)   # 81^3
+    p = T.params(order_n=n, mask_radius=r, n_rot_base=2048, dprime=4)
+    m = T.Matcher(ctx, tmpl, p, vol.shape)
+    m.run(dev(vol))
+    torch.cuda.synchronize()
+    pk, _ = T.ttm_find_peaks(m.plan, m.frob, 27, 2 * r)
+    assert pk.size == 27
+    Z, Y, X = vol.shape
+
+    def zyx(i):
+        i = np.asarray(i)
+        return np.stack([i // (Y * X), (i // X) % Y, i % X], axis=1).astype(float)
+
+    cen = np.asarray(pl.centres, dtype=float)
+    d = np.linalg.norm(zyx(pk)[:, None, :] - cen[None, :, :], axis=2)
+    assert d.min(axis=1).max() <= 3.0
+    ridx, rq, _ = T.ttm_refine_peaks(m.plan, dev(tmpl), m.orient, pk, 3.0)
+    d = np.linalg.norm(zyx(ridx)[:, None, :] - cen[None, :, :], axis=2)
+    j = d.argmin(axis=1)
+    assert d.min(axis=1).max() == 0.0
+    assert sorted(j.tolist()) == list(range(27))          # every copy exactly once
+    err = rot_angle_deg(rq, np.asarray(pl.quats)[j])
+    assert err.max() <= 1.0, err
