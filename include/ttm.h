@@ -44,7 +44,7 @@ typedef enum {
     TTM_E_UNSUPPORTED = 3, /* order n / d' / precision not built */
     TTM_E_OOM = 4,         /* device allocation failed in a *_create call */
     TTM_E_CUDA = 5,        /* a CUDA runtime call failed (message in ttm_last_error) */
-    TTM_E_TIMEOUT = 6,     /* a bounded device wait expired */
+    TTM_E_TIMEOUT = 6,     /* a bounded device wait expired (ttm_ctx_device_status) */
     TTM_E_INTERNAL = 7
 } ttm_status;
 
@@ -100,6 +100,21 @@ ttm_status ttm_ctx_create(int device, ttm_ctx** out);
 void ttm_ctx_destroy(ttm_ctx* ctx);
 /* Text of the last failure on this context ("" if none). Owned by ctx. */
 const char* ttm_last_error(const ttm_ctx* ctx);
+/* Bounded device waits (no paper counterpart; failure detection). Kernels
+ * of this library that wait on asynchronous copies (the TMA-staged fused z
+ * pass of ttm_correlate, tm_correlate and the batch) poll each wait at most
+ * `polls` times (default 4194304, far beyond a copy's microseconds). When a
+ * wait expires the kernel records it in the context, waits with a fixed
+ * limit for its own copies in flight and returns without writing its
+ * output; the context stays usable.
+ *   ttm_ctx_set_wait_limit: sets the poll limit (>= 0; 0 makes every such
+ *     wait expire at once, which exercises the error path).
+ *   ttm_ctx_device_status: synchronises `stream` and returns TTM_E_TIMEOUT
+ *     if a bounded wait of this context expired since the last check (the
+ *     outputs of the calls in between are undefined), else TTM_OK; clears
+ *     the record. */
+ttm_status ttm_ctx_set_wait_limit(ttm_ctx* ctx, int64_t polls);
+ttm_status ttm_ctx_device_status(ttm_ctx* ctx, void* stream);
 /* binom(n + d' - 1, n): the number of independent components (Sec. 3). */
 int ttm_num_components(int order_n, int dprime);
 /* Library version string, e.g. "ttm 0.1 sm_103a". */

@@ -83,6 +83,8 @@ extern "C" ttm_status ttm_ctx_create(int device, ttm_ctx** out)
         upload_probe_tables(c);
         upload_probe_tables4(c);
         c->peak_scratch = peak_scratch_address();
+        c->dev_err.alloc(sizeof(int));
+        TTM_CUDA_TRY(cudaMemset(c->dev_err.p, 0, sizeof(int)));
         *out = c;
         return TTM_OK;
     } catch (const Error& e) {
@@ -145,5 +147,31 @@ extern "C" ttm_status ttm_plan_stage_times(ttm_plan* plan, double* ms, int n)
         return TTM_OK;
     } catch (const Error& e) {
         return (ttm_status)fail(plan->ctx, e);
+    }
+}
+
+extern "C" ttm_status ttm_ctx_set_wait_limit(ttm_ctx* ctx, int64_t polls)
+{
+    if (!ctx || polls < 0) return TTM_E_INVALID_ARG;
+    ctx->wait_limit = (long long)polls;
+    return TTM_OK;
+}
+
+extern "C" ttm_status ttm_ctx_device_status(ttm_ctx* ctx, void* stream)
+{
+    if (!ctx) return TTM_E_INVALID_ARG;
+    try {
+        TTM_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        int flag = 0;
+        TTM_CUDA_TRY(cudaMemcpyAsync(&flag, ctx->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!flag) return TTM_OK;
+        TTM_CUDA_TRY(cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        throw Error{E_TIMEOUT, "a bounded device wait expired: the outputs of the calls since the last check are "
+                               "undefined"};
+    } catch (const Error& e) {
+        return (ttm_status)fail(ctx, e);
     }
 }

@@ -95,7 +95,8 @@ static void batch_capture(ttm_batch* B)
             float* C = B->cbuf[T.branch]->as<float>();
             for (int ii : T.items) {
                 BatchItem& I = *B->items[ii];
-                passes_fp32(T.prep, B->K, I.spec.as<float2>(), work, C, st);
+                const DeviceWait dw = B->ctx->wait();
+                passes_fp32(T.prep, B->K, I.spec.as<float2>(), work, C, st, &dw);
                 peakmap_box_run(B->ctx, B->fp.order_n, C, T.w[0], T.w[1], T.w[2], T.box, T.t[0], T.t[1], T.t[2],
                                 I.score, I.orient, I.frob, st);
             }

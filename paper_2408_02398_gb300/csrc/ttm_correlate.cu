@@ -12,6 +12,7 @@
 // x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "fft_reg.cuh"
@@ -180,8 +181,11 @@ struct SinkNormaliseScaled {
 
 template <typename TS, typename TW>
 void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
-                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st)
+                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st, const DeviceWait* dw)
 {
+    if constexpr (std::is_same<TS, float2>::value && std::is_same<TW, float2>::value) {
+        if (dw && !gmax && oscale == 1.f && launch_zcorr_tma(G, spec, K, tzn, cz, ncols, out, pz, *dw, st)) return;
+    }
     if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, gmax, oscale, st)) return;
     const int Z = pz.L;
     const int ld = (Z % 2 == 0) ? Z + 1 : Z;
@@ -195,12 +199,12 @@ void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64
 }
 
 template void launch_zcorr<float2, float2>(const float2*, const float2*, int, int, int, int64_t, float2*,
-                                           const LenPlan&, const float*, float, cudaStream_t);
+                                           const LenPlan&, const float*, float, cudaStream_t, const DeviceWait*);
 template void launch_zcorr<__half2, __half2>(const float2*, const __half2*, int, int, int, int64_t, __half2*,
-                                             const LenPlan&, const float*, float, cudaStream_t);
+                                             const LenPlan&, const float*, float, cudaStream_t, const DeviceWait*);
 template void launch_zcorr<__nv_bfloat162, __nv_bfloat162>(const float2*, const __nv_bfloat162*, int, int, int,
                                                            int64_t, __nv_bfloat162*, const LenPlan&, const float*,
-                                                           float, cudaStream_t);
+                                                           float, cudaStream_t, const DeviceWait*);
 
 // FP32 partial template spectra of all K components on the grid of p
 // (scaled by 1 / V of the working grid), p.zc as scratch
@@ -222,12 +226,12 @@ void spectra_fp32(Prep& p, int K, const double* d_field, float2* spec, cudaStrea
 
 // the three K-component passes of the FP32 correlate (after the per-image
 // preparation of p): fused z pass, y pass, x pass with the w epilogue
-void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st)
+void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st, const DeviceWait* dw)
 {
     const int Z = p.Z, Y = p.Y, X = p.X, Xh = p.Xh;
     const int64_t ncols = (int64_t)Y * Xh;
     const int64_t V = (int64_t)Z * Y * X;
-    launch_zcorr(p.G.as<float2>(), spec, K, p.tz, p.tz / 2, ncols, work, p.pz32, (const float*)nullptr, 1.f, st);
+    launch_zcorr(p.G.as<float2>(), spec, K, p.tz, p.tz / 2, ncols, work, p.pz32, (const float*)nullptr, 1.f, st, dw);
     launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                   StoreTo<float>{work, ncols, Xh}, st);
     launch_c2r_any<float>(work, (int64_t)Z * Y, SinkNormalise{C, p.w.as<float>(), V, X}, p.px32, K, st);
@@ -340,8 +344,9 @@ void correlate_run(ttm_plan* P, const float* d_tomo, float* d_C, cudaStream_t st
         return;
     }
     float2* work = P->work.as<float2>();
+    const DeviceWait dw = P->ctx->wait();
     launch_zcorr(p.G.as<float2>(), P->spec.as<float2>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32,
-                 (const float*)nullptr, 1.f, st);
+                 (const float*)nullptr, 1.f, st, &dw);
     stage_end(P, ST_ZCORR, st);
     launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                   StoreTo<float>{work, ncols, Xh}, st);

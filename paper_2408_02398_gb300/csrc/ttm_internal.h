@@ -59,16 +59,28 @@ enum Stage { ST_FILTER = 0, ST_SPECTRUM, ST_LOCALSUM, ST_ZCORR, ST_YPASS, ST_XPA
 void stage_begin(ttm_plan* P, cudaStream_t st);
 void stage_end(ttm_plan* P, int stage, cudaStream_t st);
 
+// bounded device waits: the context's sticky error word and poll limit
+struct DeviceWait {
+    int* err = nullptr;
+    long long limit = 0;
+};
+
 // fused z pass of the correlation (spectrum / output storage float2, or
-// FP16 / BF16 pairs with the image spectrum scaled by 1 / *gmax)
+// FP16 / BF16 pairs with the image spectrum scaled by 1 / *gmax); with a
+// DeviceWait, FP32 spectra go through the TMA-staged kernel where it
+// applies (register length <= 256, even column count)
 template <typename TS, typename TW>
 void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
-                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st);
+                  const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st,
+                  const DeviceWait* dw = nullptr);
+bool launch_zcorr_tma(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
+                      const LenPlan& pz, const DeviceWait& dw, cudaStream_t st);
 
 // FP32 partial template spectra (K components) on the grid of p, and the
 // three K-component passes of the FP32 correlate into C [K][Z][Y][X]
 void spectra_fp32(Prep& p, int K, const double* d_field, float2* spec, cudaStream_t st);
-void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st);
+void passes_fp32(Prep& p, int K, const float2* spec, float2* work, float* C, cudaStream_t st,
+                 const DeviceWait* dw = nullptr);
 // plain maximiser over box b of C (grid Z x Yin x Xin), maps written on a
 // Zo x Yout x Xout grid at the same coordinates
 void peakmap_box_run(ttm_ctx* ctx, int n, const float* C, int Z, int Yin, int Xin, const int* b, int Zo, int Yout,
@@ -131,6 +143,11 @@ struct ttm_ctx {
     ttm::DevBuf probe4;        // quaternion maximiser: probe quaternions and FP16 monomials
     size_t probe4_off[4] = {0, 0, 0, 0};
     void* peak_scratch = nullptr;  // device address of the allocation-free Find Peaks scratch
+    // sticky record of an expired bounded device wait (int, device) and the
+    // poll limit of such waits
+    ttm::DevBuf dev_err;
+    long long wait_limit = 1ll << 22;
+    ttm::DeviceWait wait() { return ttm::DeviceWait{dev_err.as<int>(), wait_limit}; }
 };
 
 struct ttm_plan {

@@ -126,7 +126,8 @@ extern "C" ttm_status tm_correlate(ttm_ctx* ctx, const float* d_tomo, int Z, int
             launch_r2c_any<float>(SrcTemplateRows{rot.as<float>(), Y, X, ty, tx}, (int64_t)tz * Y, pt, p.px32, st);
             launch_strided_any<float, -1>(pt, StridedAxis{Xh, tz, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{pt, ncols, Xh}, st);
-            launch_zcorr(p.G.as<float2>(), pt, 1, tz, tz / 2, ncols, wk, p.pz32, (const float*)nullptr, 1.f, st);
+            const DeviceWait dw = ctx->wait();
+            launch_zcorr(p.G.as<float2>(), pt, 1, tz, tz / 2, ncols, wk, p.pz32, (const float*)nullptr, 1.f, st, &dw);
             launch_strided_any<float, +1>(wk, StridedAxis{Xh, Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                       StoreTo<float>{wk, ncols, Xh}, st);
             launch_c2r_any<float>(wk, (int64_t)Z * Y, SinkTMMax{p.w.as<float>(), d_best, d_best_idx, X, (int32_t)j},

@@ -25,7 +25,7 @@ TTM_LOCALSUM_FP64, TTM_LOCALSUM_DF64 = 0, 1
 TTM_BATCH_AUTOTUNE, TTM_BATCH_LOCALSUM_DF64 = 1, 2
 
 # every symbol include/ttm.h declares
-EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_last_error", "ttm_num_components",
+EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_ctx_set_wait_limit", "ttm_ctx_device_status", "ttm_last_error", "ttm_num_components",
            "ttm_version", "ttm_rotation_set", "ttm_build_tensor_field", "ttm_plan_create", "ttm_plan_destroy",
            "ttm_plan_components", "ttm_plan_valid_box", "ttm_correlate", "ttm_plan_copy_w", "ttm_peak_map",
            "ttm_find_peaks", "tm_correlate", "ttm_plan_enable_timing", "ttm_plan_stage_times", "ttm_num_stages",
@@ -67,6 +67,8 @@ def lib():
             "ttm_default_params": (None, [C.POINTER(ttm_field_params)]),
             "ttm_ctx_create": (_i, [_i, C.POINTER(_vp)]),
             "ttm_ctx_destroy": (None, [_vp]),
+            "ttm_ctx_set_wait_limit": (_i, [_vp, _i64]),
+            "ttm_ctx_device_status": (_i, [_vp, _vp]),
             "ttm_last_error": (C.c_char_p, [_vp]),
             "ttm_num_components": (_i, [_i, _i]),
             "ttm_version": (C.c_char_p, []),
@@ -209,6 +211,16 @@ class Context:
 
 def ttm_ctx_create(device: int = 0) -> Context:
     return Context(device)
+
+
+def ttm_ctx_set_wait_limit(ctx: Context, polls: int):
+    ctx.check(lib().ttm_ctx_set_wait_limit(ctx.h, int(polls)))
+
+
+def ttm_ctx_device_status(ctx: Context, stream=None):
+    """Raises TTMError (code TTM_E_TIMEOUT) if a bounded device wait of the
+    context expired since the last check; synchronises the stream."""
+    ctx.check(lib().ttm_ctx_device_status(ctx.h, _stream(stream)))
 
 
 def ttm_build_tensor_field(ctx: Context, d_tmpl, p: ttm_field_params, d_field, stream=None):
