@@ -274,6 +274,15 @@ ttm_status ttm_mlp_loss_grad(ttm_mlp* mlp, const float* d_X, const float* d_U, i
  * the last batch of the last epoch. Blocking; allocates its permutation. */
 ttm_status ttm_mlp_train(ttm_mlp* mlp, const float* d_X, const float* d_U, int64_t n, int epochs,
                          int batch, float lr, uint64_t seed, double* h_last_loss, void* stream);
+/* Arithmetic of the forward and backward products of ttm_mlp_forward,
+ * ttm_mlp_loss_grad and ttm_mlp_train:
+ *   TTM_MLP_FP32 (default): FP32 operands and accumulation (the mode whose
+ *     gradient is checked against an FP64 reference);
+ *   TTM_MLP_BF16: operands rounded to BF16 and multiplied on the tensor
+ *     cores with FP32 accumulation (mixed-precision training); parameters,
+ *     gradients, activations between layers and the Adam state stay FP32. */
+typedef enum { TTM_MLP_FP32 = 0, TTM_MLP_BF16 = 1 } ttm_mlp_precision;
+ttm_status ttm_mlp_set_precision(ttm_mlp* mlp, int mode);
 /* BF16 tensor-core inference (the arithmetic of the learned maximiser):
  * d_U [n][3] from d_X [n][K]; K <= 32. */
 ttm_status ttm_mlp_infer(ttm_mlp* mlp, const float* d_X, int64_t n, float* d_U, void* stream);
@@ -383,11 +392,29 @@ int ttm_merge_peaks(int64_t n, const int64_t* idx, const float* val, int Z, int 
  * differ by the rounding of the different FFT lengths.
  *   d_field   float64 [K][tz][ty][tx] (device), params as for ttm_plan_create
  *   h_idx, h_val  P entries (host): tomogram linear indices and map values
- * Allocates the slab workspace (per call); synchronises `stream`. */
+ * One call: ttm_blocked_create, ttm_blocked_run, ttm_blocked_destroy
+ * (allocates the slab workspace for the call); synchronises `stream`. */
 ttm_status ttm_blocked_peaks(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
                              const ttm_field_params* params, const float* h_tomo, int Z, int Y, int X, int slab_z,
                              int map_kind, int P, double min_dist, int64_t* h_idx, float* h_val, int* h_count,
                              void* stream);
+
+/* The same block processing as a session kept across tomograms of one
+ * shape (no paper counterpart: an execution scheme). ttm_blocked_create
+ * computes the slab table, one plan per distinct slab depth (the template
+ * spectra on each slab's working grid) and the slab buffers; allocates,
+ * blocking. ttm_blocked_run processes one Z x Y x X host tomogram: slab
+ * k + 1 is uploaded on the session's own copy stream while the kernels of
+ * slab k run on `stream` (the copies overlap the kernels when h_tomo is
+ * pinned host memory), the candidates of all slabs are gathered on the
+ * device and read back once, then merged (ttm_merge_peaks); synchronises
+ * `stream`. Runs of one session must not overlap. */
+typedef struct ttm_blocked ttm_blocked;
+ttm_status ttm_blocked_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                              const ttm_field_params* params, int Z, int Y, int X, int slab_z, ttm_blocked** out);
+ttm_status ttm_blocked_run(ttm_blocked* session, const float* h_tomo, int map_kind, int P, double min_dist,
+                           int64_t* h_idx, float* h_val, int* h_count, void* stream);
+void ttm_blocked_destroy(ttm_blocked* session);
 
 /* ------------------------------------------------------- step a6: Eqs. 1, 6, 7 */
 

@@ -17,10 +17,12 @@
 namespace ttm {
 
 // candidates at z in [cz0, cz1) (and the y, x box), neighbours tested
-// within [nz0, nz1) (and the same y, x box); indices on the Z x Y x X grid
+// within [nz0, nz1) (and the same y, x box) of a map on a Z x Y x X grid;
+// indices written on the tomogram's grid: ((z + zoff) Yt + y) Xt + x
 __global__ void k_localmax_slab(const float* __restrict__ s, int Y, int X, int cz0, int cz1, int nz0, int nz1,
-                                int y0, int y1, int x0, int x1, int64_t cap, int64_t* __restrict__ idx,
-                                float* __restrict__ val, unsigned long long* __restrict__ count)
+                                int y0, int y1, int x0, int x1, int64_t zoff, int Yt, int Xt, int64_t cap,
+                                int64_t* __restrict__ idx, float* __restrict__ val,
+                                unsigned long long* __restrict__ count)
 {
     const int bx = x1 - x0, by = y1 - y0, bz = cz1 - cz0;
     const int64_t n = (int64_t)bx * by * bz;
@@ -46,11 +48,38 @@ __global__ void k_localmax_slab(const float* __restrict__ s, int Y, int X, int c
                 }
         if (!is_max) continue;
         const unsigned long long pos = atomicAdd(count, 1ull);
-        if ((int64_t)pos < cap) { idx[pos] = i; val[pos] = v; }
+        if ((int64_t)pos < cap) {
+            idx[pos] = (((int64_t)z + zoff) * Yt + y) * Xt + x;
+            val[pos] = v;
+        }
     }
 }
 
 }  // namespace ttm
+
+// A block-processing session: the slab table, one plan per distinct slab
+// depth (template spectra on each slab's autotuned working grid), the slab
+// buffers and a copy stream, kept from one ttm_blocked_run to the next.
+struct ttm_blocked {
+    ttm_ctx* ctx = nullptr;
+    int Z = 0, Y = 0, X = 0, tz = 0, ty = 0, tx = 0, K = 0, dprime = 3;
+    int ns = 0;
+    std::vector<int> sl;
+    std::map<int, ttm_plan*> plans;
+    ttm::DevBuf d_tomo[2], d_C, d_map, d_aux, d_orient, cand, cnt;
+    int64_t cap = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    ~ttm_blocked()
+    {
+        for (auto& kv : plans) ttm_plan_destroy(kv.second);
+        for (int b = 0; b < 2; b++) {
+            if (copied[b]) cudaEventDestroy(copied[b]);
+            if (consumed[b]) cudaEventDestroy(consumed[b]);
+        }
+        if (copy_st) cudaStreamDestroy(copy_st);
+    }
+};
 
 using namespace ttm;
 
@@ -104,44 +133,36 @@ extern "C" int ttm_merge_peaks(int64_t n, const int64_t* idx, const float* val, 
     return got;
 }
 
-extern "C" ttm_status ttm_blocked_peaks(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
-                                        const ttm_field_params* params, const float* h_tomo, int Z, int Y, int X,
-                                        int slab_z, int map_kind, int P, double min_dist, int64_t* h_idx,
-                                        float* h_val, int* h_count, void* stream)
+extern "C" ttm_status ttm_blocked_create(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                                         const ttm_field_params* params, int Z, int Y, int X, int slab_z,
+                                         ttm_blocked** out)
 {
     if (!ctx) return TTM_E_INVALID_ARG;
+    ttm_blocked* B = nullptr;
     try {
-        TTM_REQUIRE(d_field && params && h_tomo && h_count && (P == 0 || (h_idx && h_val)), E_INVALID_ARG,
-                    "null pointer argument");
-        TTM_REQUIRE(P >= 0 && min_dist >= 0 && slab_z > 0 && (map_kind == 0 || map_kind == 1), E_INVALID_ARG,
-                    "bad P, min_dist, slab_z or map_kind");
+        TTM_REQUIRE(d_field && params && out, E_INVALID_ARG, "null pointer argument");
+        TTM_REQUIRE(slab_z > 0, E_INVALID_ARG, "slab_z must be positive");
         TTM_REQUIRE(Z >= tz && Y >= ty && X >= tx, E_SHAPE, "tomogram smaller than the template");
         TTM_CUDA_TRY(cudaSetDevice(ctx->device));
-        cudaStream_t st = (cudaStream_t)stream;
-        const int ns = ttm_slab_ranges(Z, tz, slab_z, nullptr, 0);
-        std::vector<int> sl(6 * (size_t)ns);
-        ttm_slab_ranges(Z, tz, slab_z, sl.data(), ns);
+        B = new ttm_blocked();
+        B->ctx = ctx;
+        B->Z = Z; B->Y = Y; B->X = X; B->tz = tz; B->ty = ty; B->tx = tx;
+        B->K = ttm_num_components(params->order_n, params->dprime);
+        B->dprime = params->dprime;
+        B->ns = ttm_slab_ranges(Z, tz, slab_z, nullptr, 0);
+        TTM_REQUIRE(B->ns > 0, E_SHAPE, "no valid z plane");
+        B->sl.resize(6 * (size_t)B->ns);
+        ttm_slab_ranges(Z, tz, slab_z, B->sl.data(), B->ns);
         const int cy = ty / 2, cx = tx / 2;
-        const int y0 = cy, y1 = Y - (ty - cy) + 1, x0 = cx, x1 = X - (tx - cx) + 1;
-        const int K = ttm_num_components(params->order_n, params->dprime);
-        // one plan per slab depth (first, middle and last slabs can differ)
-        std::map<int, ttm_plan*> plans;
-        struct PlanGuard {
-            std::map<int, ttm_plan*>& m;
-            ~PlanGuard() { for (auto& kv : m) ttm_plan_destroy(kv.second); }
-        } guard{plans};
-        DevBuf d_tomo, d_C, d_map, d_orient, d_aux, cand, cnt;
-        int max_zs = 0;
-        for (int s = 0; s < ns; s++) max_zs = std::max(max_zs, sl[6 * (size_t)s + 5] - sl[6 * (size_t)s + 4]);
-        d_tomo.alloc((size_t)max_zs * Y * X * sizeof(float));
-        size_t cap_vox = 0;
-        std::vector<int64_t> all_idx;
-        std::vector<float> all_val;
-        for (int s = 0; s < ns; s++) {
-            const int* r = &sl[6 * (size_t)s];
-            const int o0 = r[0], o1 = r[1], m0 = r[2], m1 = r[3], i0 = r[4], i1 = r[5];
-            const int Zs = i1 - i0;
-            ttm_plan*& plan = plans[Zs];
+        const int64_t by = Y - (ty - cy) + 1 - cy, bx = X - (tx - cx) + 1 - cx;
+        size_t max_in = 0, max_work = 0;
+        for (int s = 0; s < B->ns; s++) {
+            const int* r = &B->sl[6 * (size_t)s];
+            const int Zs = r[5] - r[4];
+            max_in = std::max(max_in, (size_t)Zs * Y * X);
+            // strict 26-neighbour maxima: at most one per 2 x 2 x 2 cell
+            B->cap += ((r[1] - r[0]) / 2 + 1) * (by / 2 + 1) * (bx / 2 + 1);
+            ttm_plan*& plan = B->plans[Zs];
             if (!plan) {
                 int work[3];
                 const int t3[3] = {Zs, Y, X};
@@ -151,58 +172,110 @@ extern "C" ttm_status ttm_blocked_peaks(ttm_ctx* ctx, const double* d_field, int
                 if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
             }
             const Prep& p = plan->prep;
-            const size_t Vw = (size_t)p.Z * p.Y * p.X;
-            if (Vw > cap_vox) {  // grow the per-slab buffers to the largest working grid
-                cap_vox = Vw;
-                d_C.alloc(Vw * K * sizeof(float));
-                d_map.alloc(Vw * sizeof(float));
-                d_aux.alloc(Vw * sizeof(float));
-                d_orient.alloc(Vw * params->dprime * sizeof(float));
-                cand.alloc((Vw / 8 + 64) * (sizeof(int64_t) + sizeof(float)));
-                cnt.alloc(sizeof(unsigned long long));
-            }
-            TTM_CUDA_TRY(cudaMemcpyAsync(d_tomo.p, h_tomo + (size_t)i0 * Y * X, (size_t)Zs * Y * X * sizeof(float),
-                                         cudaMemcpyHostToDevice, st));
-            ttm_status rc = ttm_correlate(plan, d_tomo.as<float>(), d_C.as<float>(), stream);
-            if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
-            float* score = map_kind == 0 ? d_map.as<float>() : d_aux.as<float>();
-            float* frob = map_kind == 1 ? d_map.as<float>() : d_aux.as<float>();
-            rc = ttm_peak_map(plan, d_C.as<float>(), TTM_MAX_PLAIN, nullptr, score, d_orient.as<float>(), frob, stream);
-            if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
-            // local maxima of the output planes, on the slab's working grid
-            const int64_t cap = (int64_t)(cand.bytes / (sizeof(int64_t) + sizeof(float)));
-            int64_t* cidx = cand.as<int64_t>();
-            float* cval = reinterpret_cast<float*>(cidx + cap);
-            TTM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), st));
-            k_localmax_slab<<<4 * 152 * 8, 256, 0, st>>>(d_map.as<float>(), p.Y, p.X, o0 - i0, o1 - i0, m0 - i0,
-                                                          m1 - i0, y0, y1, x0, x1, cap, cidx, cval,
-                                                          cnt.as<unsigned long long>());
-            TTM_LAUNCH_CHECK();
-            unsigned long long n = 0;
-            TTM_CUDA_TRY(cudaMemcpyAsync(&n, cnt.p, sizeof(n), cudaMemcpyDeviceToHost, st));
-            TTM_CUDA_TRY(cudaStreamSynchronize(st));
-            TTM_REQUIRE((int64_t)n <= cap, E_INTERNAL, "peak candidate buffer overflow");
-            std::vector<int64_t> li(n);
-            std::vector<float> lv(n);
-            if (n) {
-                TTM_CUDA_TRY(cudaMemcpyAsync(li.data(), cidx, n * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-                TTM_CUDA_TRY(cudaMemcpyAsync(lv.data(), cval, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-                TTM_CUDA_TRY(cudaStreamSynchronize(st));
-            }
-            // slab working-grid index -> tomogram index
-            for (size_t k = 0; k < n; k++) {
-                const int64_t i = li[k];
-                const int64_t x = i % p.X, y = (i / p.X) % p.Y, z = i / ((int64_t)p.X * p.Y);
-                all_idx.push_back(((z + i0) * Y + y) * X + x);
-                all_val.push_back(lv[k]);
-            }
+            max_work = std::max(max_work, (size_t)p.Z * p.Y * p.X);
         }
-        const int got = ttm_merge_peaks((int64_t)all_idx.size(), all_idx.data(), all_val.data(), Z, Y, X, P,
-                                        min_dist, h_idx, h_val);
+        for (int b = 0; b < 2; b++) {
+            B->d_tomo[b].alloc(max_in * sizeof(float));
+            TTM_CUDA_TRY(cudaEventCreateWithFlags(&B->copied[b], cudaEventDisableTiming));
+            TTM_CUDA_TRY(cudaEventCreateWithFlags(&B->consumed[b], cudaEventDisableTiming));
+        }
+        TTM_CUDA_TRY(cudaStreamCreateWithFlags(&B->copy_st, cudaStreamNonBlocking));
+        B->d_C.alloc(max_work * B->K * sizeof(float));
+        B->d_map.alloc(max_work * sizeof(float));
+        B->d_aux.alloc(max_work * sizeof(float));
+        B->d_orient.alloc(max_work * params->dprime * sizeof(float));
+        B->cand.alloc((size_t)B->cap * (sizeof(int64_t) + sizeof(float)));
+        B->cnt.alloc(sizeof(unsigned long long));
+        *out = B;
+        return TTM_OK;
+    } catch (const Error& e) {
+        delete B;
+        return (ttm_status)fail(ctx, e);
+    }
+}
+
+extern "C" void ttm_blocked_destroy(ttm_blocked* b) { delete b; }
+
+extern "C" ttm_status ttm_blocked_run(ttm_blocked* B, const float* h_tomo, int map_kind, int P, double min_dist,
+                                      int64_t* h_idx, float* h_val, int* h_count, void* stream)
+{
+    if (!B) return TTM_E_INVALID_ARG;
+    ttm_ctx* ctx = B->ctx;
+    try {
+        TTM_REQUIRE(h_tomo && h_count && (P == 0 || (h_idx && h_val)), E_INVALID_ARG, "null pointer argument");
+        TTM_REQUIRE(P >= 0 && min_dist >= 0 && (map_kind == 0 || map_kind == 1), E_INVALID_ARG,
+                    "bad P, min_dist or map_kind");
+        TTM_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        const int Y = B->Y, X = B->X;
+        const int cy = B->ty / 2, cx = B->tx / 2;
+        const int y0 = cy, y1 = Y - (B->ty - cy) + 1, x0 = cx, x1 = X - (B->tx - cx) + 1;
+        int64_t* cidx = B->cand.as<int64_t>();
+        float* cval = reinterpret_cast<float*>(cidx + B->cap);
+        TTM_CUDA_TRY(cudaMemsetAsync(B->cnt.p, 0, sizeof(unsigned long long), st));
+        for (int b = 0; b < 2; b++) TTM_CUDA_TRY(cudaEventRecord(B->consumed[b], st));
+        for (int s = 0; s < B->ns; s++) {
+            const int* r = &B->sl[6 * (size_t)s];
+            const int o0 = r[0], o1 = r[1], m0 = r[2], m1 = r[3], i0 = r[4], i1 = r[5];
+            const int Zs = i1 - i0;
+            const int b = s & 1;
+            ttm_plan* plan = B->plans.at(Zs);
+            // upload of this slab on the copy stream, once the correlation of
+            // the slab that last used the buffer has read it
+            TTM_CUDA_TRY(cudaStreamWaitEvent(B->copy_st, B->consumed[b], 0));
+            TTM_CUDA_TRY(cudaMemcpyAsync(B->d_tomo[b].p, h_tomo + (size_t)i0 * Y * X,
+                                         (size_t)Zs * Y * X * sizeof(float), cudaMemcpyHostToDevice, B->copy_st));
+            TTM_CUDA_TRY(cudaEventRecord(B->copied[b], B->copy_st));
+            TTM_CUDA_TRY(cudaStreamWaitEvent(st, B->copied[b], 0));
+            ttm_status rc = ttm_correlate(plan, B->d_tomo[b].as<float>(), B->d_C.as<float>(), stream);
+            if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
+            TTM_CUDA_TRY(cudaEventRecord(B->consumed[b], st));
+            float* score = map_kind == 0 ? B->d_map.as<float>() : B->d_aux.as<float>();
+            float* frob = map_kind == 1 ? B->d_map.as<float>() : B->d_aux.as<float>();
+            rc = ttm_peak_map(plan, B->d_C.as<float>(), TTM_MAX_PLAIN, nullptr, score, B->d_orient.as<float>(), frob,
+                              stream);
+            if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
+            const Prep& p = plan->prep;
+            k_localmax_slab<<<4 * 152 * 8, 256, 0, st>>>(B->d_map.as<float>(), p.Y, p.X, o0 - i0, o1 - i0, m0 - i0,
+                                                          m1 - i0, y0, y1, x0, x1, (int64_t)i0, Y, X, B->cap, cidx,
+                                                          cval, B->cnt.as<unsigned long long>());
+            TTM_LAUNCH_CHECK();
+        }
+        unsigned long long n = 0;
+        TTM_CUDA_TRY(cudaMemcpyAsync(&n, B->cnt.p, sizeof(n), cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        TTM_REQUIRE((int64_t)n <= B->cap, E_INTERNAL, "peak candidate buffer overflow");
+        std::vector<int64_t> li(n);
+        std::vector<float> lv(n);
+        if (n) {
+            TTM_CUDA_TRY(cudaMemcpyAsync(li.data(), cidx, n * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            TTM_CUDA_TRY(cudaMemcpyAsync(lv.data(), cval, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+            TTM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        const int got = ttm_merge_peaks((int64_t)n, li.data(), lv.data(), B->Z, Y, X, P, min_dist, h_idx, h_val);
         TTM_REQUIRE(got >= 0, E_INTERNAL, "merge failed");
         *h_count = got;
         return TTM_OK;
     } catch (const Error& e) {
         return (ttm_status)fail(ctx, e);
     }
+}
+
+extern "C" ttm_status ttm_blocked_peaks(ttm_ctx* ctx, const double* d_field, int tz, int ty, int tx,
+                                        const ttm_field_params* params, const float* h_tomo, int Z, int Y, int X,
+                                        int slab_z, int map_kind, int P, double min_dist, int64_t* h_idx,
+                                        float* h_val, int* h_count, void* stream)
+{
+    if (!ctx) return TTM_E_INVALID_ARG;
+    if (!h_tomo || !h_count || (P > 0 && (!h_idx || !h_val)) || P < 0 || min_dist < 0 ||
+        (map_kind != 0 && map_kind != 1)) {
+        ctx->last_error = "bad argument";
+        return TTM_E_INVALID_ARG;
+    }
+    ttm_blocked* B = nullptr;
+    ttm_status rc = ttm_blocked_create(ctx, d_field, tz, ty, tx, params, Z, Y, X, slab_z, &B);
+    if (rc != TTM_OK) return rc;
+    rc = ttm_blocked_run(B, h_tomo, map_kind, P, min_dist, h_idx, h_val, h_count, stream);
+    ttm_blocked_destroy(B);
+    return rc;
 }

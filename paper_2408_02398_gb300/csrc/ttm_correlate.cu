@@ -12,7 +12,6 @@
 // x pass (complex-to-real) whose epilogue multiplies by w(x) and writes C.
 
 #include <algorithm>
-#include <type_traits>
 #include <vector>
 
 #include "fft_reg.cuh"
@@ -183,9 +182,7 @@ template <typename TS, typename TW>
 void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
                   const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st, const DeviceWait* dw)
 {
-    if constexpr (std::is_same<TS, float2>::value && std::is_same<TW, float2>::value) {
-        if (dw && !gmax && oscale == 1.f && launch_zcorr_tma(G, spec, K, tzn, cz, ncols, out, pz, *dw, st)) return;
-    }
+    if (dw && launch_zcorr_tma(G, spec, K, tzn, cz, ncols, out, pz, gmax, oscale, *dw, st)) return;
     if (launch_zcorr_fs(G, spec, K, tzn, cz, ncols, out, pz, gmax, oscale, st)) return;
     const int Z = pz.L;
     const int ld = (Z % 2 == 0) ? Z + 1 : Z;
@@ -307,8 +304,9 @@ static void correlate_passes16(ttm_plan* P, float* d_C, cudaStream_t st)
         p.G.as<float2>(), Z * ncols, reinterpret_cast<unsigned int*>(gmax));
     TTM_LAUNCH_CHECK();
     T16* work = P->work.as<T16>();
+    const DeviceWait dw = P->ctx->wait();
     launch_zcorr(p.G.as<float2>(), P->spec.as<T16>(), P->K, p.tz, p.tz / 2, ncols, work, p.pz32,
-                 (const float*)gmax, P->work_qz, st);
+                 (const float*)gmax, P->work_qz, st, &dw);
     stage_end(P, ST_ZCORR, st);
     launch_strided_any<float, +1>(work, StridedAxis{Xh, (int64_t)P->K * Z, ncols, Xh}, p.py32, ProIdentity<float>(),
                                   StoreTo16<T16>{work, ncols, Xh, P->work_q}, st);

@@ -67,14 +67,15 @@ struct DeviceWait {
 
 // fused z pass of the correlation (spectrum / output storage float2, or
 // FP16 / BF16 pairs with the image spectrum scaled by 1 / *gmax); with a
-// DeviceWait, FP32 spectra go through the TMA-staged kernel where it
-// applies (register length <= 256, even column count)
+// DeviceWait, the TMA-staged kernel where it applies (register length
+// <= 256, row strides a multiple of 16 bytes)
 template <typename TS, typename TW>
 void launch_zcorr(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
                   const LenPlan& pz, const float* gmax, float oscale, cudaStream_t st,
                   const DeviceWait* dw = nullptr);
-bool launch_zcorr_tma(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
-                      const LenPlan& pz, const DeviceWait& dw, cudaStream_t st);
+template <typename TS, typename TW>
+bool launch_zcorr_tma(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
+                      const LenPlan& pz, const float* gmax, float oscale, const DeviceWait& dw, cudaStream_t st);
 
 // FP32 partial template spectra (K components) on the grid of p, and the
 // three K-component passes of the FP32 correlate into C [K][Z][Y][X]
@@ -187,6 +188,7 @@ struct ttm_mlp {
     ttm::DevBuf xb, ub, a1, h1, a2, h2, y, dy, loss, part;
     ttm::DevBuf image;         // kMlpImageBytes, rebuilt when the parameters change
     bool image_dirty = true;
+    bool bf16 = false;         // forward / backward products in BF16 (tensor cores)
 };
 
 namespace ttm {

@@ -72,6 +72,63 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
         }
 }
 
+// The same product with op(A) and op(B) rounded to BF16 (nearest even) as
+// they are staged and multiplied on the tensor cores (mma.sync m16n8k16,
+// FP32 accumulate): the BF16 training mode. 64 x 64 tiles, k steps of 16;
+// warp w owns rows 16 (w >> 1) .. +16 and columns 32 (w & 1) .. +32 of the
+// tile (four 8-column MMA tiles). Shared rows of 24 BF16 (48 bytes) keep the
+// fragment loads of a warp in distinct banks.
+template <bool TA, bool TB, bool ACC>
+__global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                   const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                   int ldc)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[64][24], Bs[64][24];  // [m][k], [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int kk = e / 64, mm = e % 64;
+            const int m = m0 + mm, k = k0 + kk;
+            float a = 0.f, b = 0.f;
+            if (m < M && k < K) a = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
+            const int n = n0 + mm;
+            if (n < N && k < K) b = TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n];
+            As[mm][kk] = __float2bfloat16_rn(a);
+            Bs[mm][kk] = __float2bfloat16_rn(b);
+        }
+        __syncthreads();
+        uint32_t af[4];
+        af[0] = ld_b32(&As[wm + g][2 * t]);
+        af[1] = ld_b32(&As[wm + g + 8][2 * t]);
+        af[2] = ld_b32(&As[wm + g][2 * t + 8]);
+        af[3] = ld_b32(&As[wm + g + 8][2 * t + 8]);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int nn = wn + 8 * j + g;
+            mma_bf16(acc[j], af, ld_b32(&Bs[nn][2 * t]), ld_b32(&Bs[nn][2 * t + 8]));
+        }
+        __syncthreads();
+    }
+    // accumulator (j, 2h + q): row g + 8h, column 8j + 2t + q of the warp tile
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int m = m0 + wm + g + 8 * h, n = n0 + wn + 8 * j + 2 * t + q;
+                if (m < M && n < N) {
+                    float* c = C + (int64_t)m * ldc + n;
+                    const float v = acc[j][2 * h + q];
+                    *c = ACC ? *c + v : v;
+                }
+            }
+}
+
 __device__ __forceinline__ float gelu_t(float x)
 {
     const float c = 0.7978845608028654f;  // sqrt(2 / pi)
@@ -178,11 +235,15 @@ __global__ void k_sum_partial(const float* __restrict__ v, int64_t n, double* __
     if (threadIdx.x == 0) out[blockIdx.x] = s[0];
 }
 
+// the products of the forward and backward passes: FP32 (the mode the
+// gradient check against the FP64 oracle holds) or BF16 tensor cores
 template <bool TA, bool TB, bool ACC>
-void sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, cudaStream_t st)
+void sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, cudaStream_t st,
+           bool bf16 = false)
 {
     dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
-    k_sgemm<TA, TB, ACC><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    if (bf16) k_gemm_bf16<TA, TB, ACC><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    else k_sgemm<TA, TB, ACC><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
     TTM_LAUNCH_CHECK();
 }
 
@@ -346,15 +407,16 @@ static void mlp_forward_rows(ttm_mlp* M, const float* X, const float* U, int64_t
                              cudaStream_t st)
 {
     const int K = M->K;
+    const bool bf = M->bf16;
     MlpView w = view(M->params.as<float>(), K);
     float *a1 = M->a1.as<float>(), *h1 = M->h1.as<float>(), *a2 = M->a2.as<float>(), *h2 = M->h2.as<float>();
-    sgemm<false, true, false>((int)rows, kH, K, X, K, w.W1, K, a1, kH, st);
+    sgemm<false, true, false>((int)rows, kH, K, X, K, w.W1, K, a1, kH, st, bf);
     k_bias_gelu<<<1024, 256, 0, st>>>(a1, w.b1, h1, rows, kH);
     TTM_LAUNCH_CHECK();
-    sgemm<false, true, false>((int)rows, kH, kH, h1, kH, w.W2, kH, a2, kH, st);
+    sgemm<false, true, false>((int)rows, kH, kH, h1, kH, w.W2, kH, a2, kH, st, bf);
     k_bias_gelu<<<1024, 256, 0, st>>>(a2, w.b2, h2, rows, kH);
     TTM_LAUNCH_CHECK();
-    sgemm<false, true, false>((int)rows, 3, kH, h2, kH, w.W3, kH, M->y.as<float>(), 3, st);
+    sgemm<false, true, false>((int)rows, 3, kH, h2, kH, w.W3, kH, M->y.as<float>(), 3, st, bf);
     k_mlp_out<<<256, 256, 0, st>>>(M->y.as<float>(), w.b3, U, rows, dscale, u_out, M->dy.as<float>(),
                                    M->loss.as<float>());
     TTM_LAUNCH_CHECK();
@@ -365,6 +427,7 @@ static void mlp_forward_rows(ttm_mlp* M, const float* X, const float* U, int64_t
 static void mlp_backward_rows(ttm_mlp* M, const float* X, int64_t rows, float* g, bool acc, cudaStream_t st)
 {
     const int K = M->K;
+    const bool bf = M->bf16;
     MlpView w = view(M->params.as<float>(), K);
     float* gW1 = g;
     float* gb1 = gW1 + (size_t)kH * K;
@@ -376,26 +439,26 @@ static void mlp_backward_rows(ttm_mlp* M, const float* X, int64_t rows, float* g
     float* dy = M->dy.as<float>();
     const int r = (int)rows;
     // dW3 = dy^T h2, db3 = colsum dy
-    if (acc) sgemm<true, false, true>(3, kH, r, dy, 3, h2, kH, gW3, kH, st);
-    else sgemm<true, false, false>(3, kH, r, dy, 3, h2, kH, gW3, kH, st);
+    if (acc) sgemm<true, false, true>(3, kH, r, dy, 3, h2, kH, gW3, kH, st, bf);
+    else sgemm<true, false, false>(3, kH, r, dy, 3, h2, kH, gW3, kH, st, bf);
     k_colsum<<<1, 32, 0, st>>>(dy, rows, 3, gb3, acc);
     TTM_LAUNCH_CHECK();
     // d2 = (dy W3) * GELU'(a2), reusing h2 as storage after its last use
     float* d2 = h2;
-    sgemm<false, false, false>(r, kH, 3, dy, 3, w.W3, kH, d2, kH, st);
+    sgemm<false, false, false>(r, kH, 3, dy, 3, w.W3, kH, d2, kH, st, bf);
     k_gelu_bwd<<<1024, 256, 0, st>>>(d2, a2, rows * kH);
     TTM_LAUNCH_CHECK();
-    if (acc) sgemm<true, false, true>(kH, kH, r, d2, kH, h1, kH, gW2, kH, st);
-    else sgemm<true, false, false>(kH, kH, r, d2, kH, h1, kH, gW2, kH, st);
+    if (acc) sgemm<true, false, true>(kH, kH, r, d2, kH, h1, kH, gW2, kH, st, bf);
+    else sgemm<true, false, false>(kH, kH, r, d2, kH, h1, kH, gW2, kH, st, bf);
     k_colsum<<<1, kH, 0, st>>>(d2, rows, kH, gb2, acc);
     TTM_LAUNCH_CHECK();
     // d1 = (d2 W2) * GELU'(a1), into h1 after its last use
     float* d1 = h1;
-    sgemm<false, false, false>(r, kH, kH, d2, kH, w.W2, kH, d1, kH, st);
+    sgemm<false, false, false>(r, kH, kH, d2, kH, w.W2, kH, d1, kH, st, bf);
     k_gelu_bwd<<<1024, 256, 0, st>>>(d1, a1, rows * kH);
     TTM_LAUNCH_CHECK();
-    if (acc) sgemm<true, false, true>(kH, K, r, d1, kH, X, K, gW1, K, st);
-    else sgemm<true, false, false>(kH, K, r, d1, kH, X, K, gW1, K, st);
+    if (acc) sgemm<true, false, true>(kH, K, r, d1, kH, X, K, gW1, K, st, bf);
+    else sgemm<true, false, false>(kH, K, r, d1, kH, X, K, gW1, K, st, bf);
     k_colsum<<<1, kH, 0, st>>>(d1, rows, kH, gb1, acc);
     TTM_LAUNCH_CHECK();
 }
@@ -659,4 +722,11 @@ extern "C" ttm_status ttm_mlp_make_pairs(ttm_ctx* ctx, const float* d_C, int ord
     } catch (const Error& e) {
         return (ttm_status)fail(ctx, e);
     }
+}
+
+extern "C" ttm_status ttm_mlp_set_precision(ttm_mlp* mlp, int mode)
+{
+    if (!mlp || (mode != TTM_MLP_FP32 && mode != TTM_MLP_BF16)) return TTM_E_INVALID_ARG;
+    mlp->bf16 = mode == TTM_MLP_BF16;
+    return TTM_OK;
 }

@@ -57,30 +57,35 @@ double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<doub
 
 constexpr int kPreThreads = 256;
 
-// One voxel per thread: g = h * f from the 27-point product filter in FP32
-// (the input is FP32), written as g (f32) and as (g, g^2) in FP64 or as
-// double-float pairs for the local sums; per-block partial sums of g^2 for
-// the variance floor.
+// Four consecutive voxels of a row per thread: g = h * f from the 27-point
+// product filter in FP32 (the input is FP32): each of the 9 input rows
+// (dz, dy) is read once over x0-1 .. x0+4 and filtered along x into the
+// four outputs. Writes g (f32) and (g, g^2) in FP64 or as double-float
+// pairs for the local sums, and per-block partial sums of g^2 for the
+// variance floor (fixed order).
 // The tomogram f is Zt x Yt x Xt; g lives on the working grid Z x Y x X
 // (>= the tomogram on every axis, zero beyond it apart from the filter's
 // one-voxel spill). Only tomogram voxels enter the g^2 partial sums.
+constexpr int kPreVox = 4;
+
 template <bool DF>
 __global__ void __launch_bounds__(kPreThreads)
 k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, int X, float a,
             float* __restrict__ g32, double2* __restrict__ zc, double* __restrict__ partials)
 {
     __shared__ float warp_sums[kPreThreads / 32];
-    const int64_t V = (int64_t)Z * Y * X;
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float g = 0.f;
-    bool in_tomo = false;
-    if (v < V) {
-        const int x = (int)(v % X);
-        const int64_t t = v / X;
-        const int y = (int)(t % Y);
-        const int z = (int)(t / Y);
-        in_tomo = z < Zt && y < Yt && x < Xt;
+    const int Xq = (X + kPreVox - 1) / kPreVox;
+    const int64_t nq = (int64_t)Z * Y * Xq;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float sq = 0.f;
+    if (q < nq) {
+        const int xq = (int)(q % Xq);
+        const int64_t row = q / Xq;
+        const int y = (int)(row % Y);
+        const int z = (int)(row / Y);
+        const int x0 = xq * kPreVox;
         const float tap[3] = {a, 1.f - 2.f * a, a};
+        float g[kPreVox] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int dz = -1; dz <= 1; dz++) {
             const int zz = z + dz;
@@ -89,24 +94,36 @@ k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, i
             for (int dy = -1; dy <= 1; dy++) {
                 const int yy = y + dy;
                 if (yy < 0 || yy >= Yt) continue;
-                const float* row = f + ((int64_t)zz * Yt + yy) * Xt;
-                float r = x < Xt ? tap[1] * __ldg(row + x) : 0.f;
-                if (x > 0 && x - 1 < Xt) r += tap[0] * __ldg(row + x - 1);
-                if (x + 1 < Xt) r += tap[2] * __ldg(row + x + 1);
-                g += tap[dz + 1] * tap[dy + 1] * r;
+                const float* r = f + ((int64_t)zz * Yt + yy) * Xt;
+                float v[kPreVox + 2];
+#pragma unroll
+                for (int k = 0; k < kPreVox + 2; k++) {
+                    const int xx = x0 - 1 + k;
+                    v[k] = (xx >= 0 && xx < Xt) ? __ldg(r + xx) : 0.f;
+                }
+                const float wgt = tap[dz + 1] * tap[dy + 1];
+#pragma unroll
+                for (int k = 0; k < kPreVox; k++)
+                    g[k] += wgt * (tap[1] * v[k + 1] + tap[0] * v[k] + tap[2] * v[k + 2]);
             }
         }
-        g32[v] = g;
-        if (DF) {
-            // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
-            const df64 sq = two_prod(g, g);
-            reinterpret_cast<float4*>(zc)[v] = make_float4(g, 0.f, sq.hi, sq.lo);
-        } else {
-            const double gd = (double)g;
-            zc[v] = make_double2(gd, gd * gd);
+        const int64_t v0 = row * X + x0;
+        const bool inrow = z < Zt && y < Yt;
+#pragma unroll
+        for (int k = 0; k < kPreVox; k++) {
+            if (x0 + k >= X) break;
+            g32[v0 + k] = g[k];
+            if (DF) {
+                // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
+                const df64 s2 = two_prod(g[k], g[k]);
+                reinterpret_cast<float4*>(zc)[v0 + k] = make_float4(g[k], 0.f, s2.hi, s2.lo);
+            } else {
+                const double gd = (double)g[k];
+                zc[v0 + k] = make_double2(gd, gd * gd);
+            }
+            if (inrow && x0 + k < Xt) sq += g[k] * g[k];
         }
     }
-    float sq = in_tomo ? g * g : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = sq;
@@ -318,7 +335,7 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Zt, int Yt, int Xt, int Z, int Y, in
     p.pyd = ctx_len_plan(ctx, Y, TW_DF64);
     p.pzd = ctx_len_plan(ctx, Z, TW_DF64);
     const int64_t V = (int64_t)Z * Y * X, Vh = (int64_t)Z * Y * p.Xh;
-    p.nblk_pre = ceil_div(V, kPreThreads);
+    p.nblk_pre = ceil_div((int64_t)Z * Y * ceil_div(X, kPreVox), kPreThreads);
     p.g32.alloc(V * sizeof(float));
     p.G.alloc(Vh * sizeof(float2));
     p.zc.alloc(V * sizeof(double2));

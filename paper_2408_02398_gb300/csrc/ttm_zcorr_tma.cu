@@ -11,7 +11,8 @@
 //    TMA into the other half of a double buffer while component a is being
 //    transformed, so the per-component loads no longer stall the warps
 //    (the long-scoreboard stall of the plain-load version).
-// W is even, so every box starts on a 16-byte boundary (x = 2 c0 floats).
+// W is a multiple of 4, so every box starts on a 16-byte boundary (x = c0
+// complex values of 8 bytes, or of 4 bytes for 16-bit spectra).
 // Every wait on a copy is bounded (the context's wait limit); when one
 // expires the kernel records it in the context's error word, waits (with a
 // generous fixed limit) for the copies it has in flight and returns without
@@ -26,7 +27,7 @@ namespace ttm {
 
 template <int E, int P> struct ZtShape {
     static constexpr int L = E * P;
-    static constexpr int W = (256 / P) & ~1;  // even: 16-byte aligned boxes
+    static constexpr int W = (256 / P) & ~3;  // a multiple of 4: 16-byte aligned boxes
     static constexpr int THREADS = W * P;
     static constexpr int KS = P + 1;
     static constexpr int LD = (E * KS) | 1;
@@ -35,14 +36,15 @@ template <int E, int P> struct ZtShape {
 __host__ __device__ constexpr size_t zt_align(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
 // shared-memory layout (bytes): image tile, two template-row buffers (each
-// 128-byte aligned, the TMA destinations), twiddles, transpose, barriers
+// 128-byte aligned, the TMA destinations; es = bytes per stored complex
+// value), twiddles, transpose, barriers
 struct ZtLayout {
     size_t g, s0, s1, tw, xa, bar, total;
-    __host__ __device__ ZtLayout(int Z, int W, int LD, int tzn)
+    __host__ __device__ ZtLayout(int Z, int W, int LD, int tzn, int es)
     {
         g = 0;
         s0 = zt_align((size_t)Z * W * sizeof(float2), 128);
-        const size_t sb = zt_align((size_t)tzn * W * sizeof(float2), 128);
+        const size_t sb = zt_align((size_t)tzn * W * es, 128);
         s1 = s0 + sb;
         tw = s1 + sb;
         xa = tw + zt_align((size_t)Z * sizeof(float2), 16);
@@ -53,18 +55,23 @@ struct ZtLayout {
 
 constexpr long long kDrainPolls = 1ll << 22;
 
-template <int E, int P>
+// TS / TW: storage of the template spectra and of the output (float2, or
+// FP16 / BF16 pairs with the image spectrum scaled by 1 / *gmax as it is
+// used and the output scaled by oscale, as in the plain-load kernel)
+template <int E, int P, typename TS, typename TW>
 __global__ void __launch_bounds__(256, 2)
 k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmS, int K, int tzn, int cz,
-            int64_t ncols, float2* __restrict__ out, const void* twg, long long wait_limit, int* __restrict__ err)
+            int64_t ncols, TW* __restrict__ out, const void* twg, const float* __restrict__ gmax, float oscale,
+            long long wait_limit, int* __restrict__ err)
 {
     using S = ZtShape<E, P>;
     constexpr int Z = S::L;
     constexpr int W = S::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const ZtLayout lay(Z, W, S::LD, tzn);
+    const ZtLayout lay(Z, W, S::LD, tzn, (int)sizeof(TS));
     float2* gt = reinterpret_cast<float2*>(smem_raw + lay.g);
-    float2* sbuf[2] = {reinterpret_cast<float2*>(smem_raw + lay.s0), reinterpret_cast<float2*>(smem_raw + lay.s1)};
+    TS* sbuf[2] = {reinterpret_cast<TS*>(smem_raw + lay.s0), reinterpret_cast<TS*>(smem_raw + lay.s1)};
+    const float gsc = (gmax && *gmax > 0.f) ? 1.f / *gmax : 1.f;
     float2* tw = reinterpret_cast<float2*>(smem_raw + lay.tw);
     float2* xa = reinterpret_cast<float2*>(smem_raw + lay.xa);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + lay.bar);  // [0] image tile, [1], [2] template rows
@@ -73,7 +80,7 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
     const int64_t c0 = (int64_t)blockIdx.x * W;
     const int64_t c = c0 + w;
     const bool act = c < ncols;
-    const uint32_t sbytes = (uint32_t)(tzn * W * sizeof(float2));
+    const uint32_t sbytes = (uint32_t)(tzn * W * sizeof(TS));
     if (t == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -113,14 +120,14 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
             if (a + 1 < K) mbar_wait(&bars[1 + (buf ^ 1)], ((a + 1) >> 1) & 1, kDrainPolls);
             return;
         }
-        const float2* sp = sbuf[buf] + w;
+        const TS* sp = sbuf[buf] + w;
         float2 x[E];
 #pragma unroll
         for (int m = 0; m < E; m++) {
             // template row j lands on z = (j - cz) mod Z
             int j = p + P * m + cz;
             if (j >= Z) j -= Z;
-            x[m] = j < tzn ? sp[j * W] : make_float2(0.f, 0.f);
+            x[m] = j < tzn ? load_cx(sp[j * W]) : make_float2(0.f, 0.f);
         }
         fs_phase1<float, E, P, -1>(x, p, xl, tw);
         __syncthreads();
@@ -135,7 +142,7 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
             float2* u = x + ii * P;
             dft_reg<P, -1, S::L, float>(u, tw);
 #pragma unroll
-            for (int k2 = 0; k2 < P; k2++) u[k2] = cmulconj(gl[(k1 + E * k2) * W], u[k2]);
+            for (int k2 = 0; k2 < P; k2++) u[k2] = cmulconj(cscale(gl[(k1 + E * k2) * W], gsc), u[k2]);
             // inverse, backwards: P-point DFT over k2, conjugate twiddles
             dft_reg<P, +1, S::L, float>(u, tw);
 #pragma unroll
@@ -150,9 +157,9 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
         for (int k1 = 0; k1 < E; k1++) x[k1] = xl[k1 * S::KS + p];
         dft_reg<E, +1, S::L, float>(x, tw);
         if (act) {
-            float2* o = out + (int64_t)a * Z * ncols + c;
+            TW* o = out + (int64_t)a * Z * ncols + c;
 #pragma unroll
-            for (int m = 0; m < E; m++) o[(int64_t)(p + P * m) * ncols] = x[m];
+            for (int m = 0; m < E; m++) store_cx(o + (int64_t)(p + P * m) * ncols, cscale(x[m], oscale));
         }
         __syncthreads();  // all reads of xl and of this buffer done
     }
@@ -181,40 +188,51 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// 2-D FP32 view [rows][2 * ncols] of a complex array, box [box_rows][2 W]
-static bool make_map(CUtensorMap& m, const float2* base, int64_t ncols, int64_t rows, int W, int box_rows)
+// 2-D view [rows][ncols * es / 4] (32-bit elements) of an array of complex
+// values of es bytes (8: FP32 pairs as two FP32 elements; 4: a 16-bit pair
+// as one 32-bit element), box [box_rows][W complex values]
+static bool make_map(CUtensorMap& m, const void* base, int es, int64_t ncols, int64_t rows, int W, int box_rows)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ncols), (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)(2 * ncols * sizeof(float))};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * W), (cuuint32_t)box_rows};
+    const int per = es / 4;  // 32-bit elements per complex value
+    const cuuint64_t dims[2] = {(cuuint64_t)(per * ncols), (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ncols * es)};
+    const cuuint32_t box[2] = {(cuuint32_t)(per * W), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    return enc(&m, per == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+               const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool launch_zcorr_tma(const float2* G, const float2* spec, int K, int tzn, int cz, int64_t ncols, float2* out,
-                      const LenPlan& pz, const DeviceWait& dw, cudaStream_t st)
+template <typename TS, typename TW>
+bool launch_zcorr_tma(const float2* G, const TS* spec, int K, int tzn, int cz, int64_t ncols, TW* out,
+                      const LenPlan& pz, const float* gmax, float oscale, const DeviceWait& dw, cudaStream_t st)
 {
     int E, P;
     const int Z = pz.L;
-    if (pz.no_reg || !fs_split(Z, E, P) || Z > 256 || tzn < 1 || tzn > 256 || (ncols & 1) || !dw.err) return false;
+    constexpr int es = (int)sizeof(TS);
+    // row strides of both maps a multiple of 16 bytes
+    if (pz.no_reg || !fs_split(Z, E, P) || Z > 256 || tzn < 1 || tzn > 256 || (ncols * es) % 16 || (ncols & 1) ||
+        !dw.err)
+        return false;
     if ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(spec)) & 15) return false;
     bool launched = false;
+    // box x = c0 complex values: c0 * es bytes a multiple of 16 (c0 = block * W)
 #define TTM_ZT(E_, P_)                                                                                         \
     {                                                                                                          \
         using S = ZtShape<E_, P_>;                                                                             \
+        static_assert(S::W % 4 == 0, "tile width keeps 4-byte boxes on 16-byte boundaries");                 \
         CUtensorMap mg, ms;                                                                                    \
-        if (!make_map(mg, G, ncols, Z, S::W, Z) || !make_map(ms, spec, ncols, (int64_t)K * tzn, S::W, tzn))    \
+        if (!make_map(mg, G, 8, ncols, Z, S::W, Z) || !make_map(ms, spec, es, ncols, (int64_t)K * tzn, S::W, tzn)) \
             break;                                                                                             \
-        const size_t smem = ZtLayout(Z, S::W, S::LD, tzn).total;                                               \
+        const size_t smem = ZtLayout(Z, S::W, S::LD, tzn, es).total;                                           \
         if (smem > 110 * 1024) break;                                                                          \
-        auto k = k_zcorr_tma<E_, P_>;                                                                          \
+        auto k = k_zcorr_tma<E_, P_, TS, TW>;                                                                  \
         set_smem(k, smem);                                                                                     \
         k<<<(unsigned)ceil_div(ncols, S::W), S::THREADS, smem, st>>>(mg, ms, K, tzn, cz, ncols, out, pz.tw,  \
-                                                                       dw.limit, dw.err);                      \
+                                                                       gmax, oscale, dw.limit, dw.err);        \
         launched = true;                                                                                       \
     }
     switch (Z) {
@@ -228,5 +246,14 @@ bool launch_zcorr_tma(const float2* G, const float2* spec, int K, int tzn, int c
     if (launched) TTM_LAUNCH_CHECK();
     return launched;
 }
+
+template bool launch_zcorr_tma<float2, float2>(const float2*, const float2*, int, int, int, int64_t, float2*,
+                                               const LenPlan&, const float*, float, const DeviceWait&, cudaStream_t);
+template bool launch_zcorr_tma<__half2, __half2>(const float2*, const __half2*, int, int, int, int64_t, __half2*,
+                                                 const LenPlan&, const float*, float, const DeviceWait&,
+                                                 cudaStream_t);
+template bool launch_zcorr_tma<__nv_bfloat162, __nv_bfloat162>(const float2*, const __nv_bfloat162*, int, int, int,
+                                                               int64_t, __nv_bfloat162*, const LenPlan&,
+                                                               const float*, float, const DeviceWait&, cudaStream_t);
 
 }  // namespace ttm

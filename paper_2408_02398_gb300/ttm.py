@@ -22,6 +22,7 @@ STATUS = {0: "TTM_OK", 1: "TTM_E_INVALID_ARG", 2: "TTM_E_SHAPE", 3: "TTM_E_UNSUP
 TTM_PREC_FP32, TTM_PREC_FP16_SPECTRA, TTM_PREC_BF16_SPECTRA = 0, 1, 2
 TTM_MAX_PLAIN, TTM_MAX_MLP_WARM = 0, 1
 TTM_LOCALSUM_FP64, TTM_LOCALSUM_DF64 = 0, 1
+TTM_MLP_FP32, TTM_MLP_BF16 = 0, 1
 TTM_BATCH_AUTOTUNE, TTM_BATCH_LOCALSUM_DF64 = 1, 2
 
 # every symbol include/ttm.h declares
@@ -32,10 +33,11 @@ EXPORTS = ["ttm_default_params", "ttm_ctx_create", "ttm_ctx_destroy", "ttm_ctx_s
            "ttm_stage_name", "ttm_kernel_launches", "ttm_plan_set_localsum",
            "ttm_find_peaks_noalloc", "ttm_plan_fallback_count", "ttm_mlp_num_params", "ttm_mlp_create",
            "ttm_mlp_destroy", "ttm_mlp_inputs", "ttm_mlp_get_params", "ttm_mlp_set_params", "ttm_mlp_forward",
-           "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
+           "ttm_mlp_loss_grad", "ttm_mlp_train", "ttm_mlp_set_precision", "ttm_mlp_infer", "ttm_mlp_make_pairs", "ttm_mlp_save",
            "ttm_mlp_load", "ttm_plan_create_padded", "ttm_autotune_shape", "ttm_autotune_entries",
            "ttm_autotune_save", "ttm_autotune_load", "ttm_batch_create", "ttm_batch_run", "ttm_batch_work_shape",
-           "ttm_batch_destroy", "ttm_refine_peaks", "ttm_slab_ranges", "ttm_merge_peaks", "ttm_blocked_peaks"]
+           "ttm_batch_destroy", "ttm_refine_peaks", "ttm_slab_ranges", "ttm_merge_peaks", "ttm_blocked_peaks",
+           "ttm_blocked_create", "ttm_blocked_run", "ttm_blocked_destroy"]
 
 
 class TTMError(RuntimeError):
@@ -96,6 +98,9 @@ def lib():
             "ttm_refine_peaks": (_i, [_vp, _vp, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp]),
             "ttm_slab_ranges": (_i, [_i, _i, _i, _vp, _i]),
             "ttm_merge_peaks": (_i, [_i64, _vp, _vp, _i, _i, _i, _i, _d, _vp, _vp]),
+            "ttm_blocked_create": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _i, _i, _i, C.POINTER(_vp)]),
+            "ttm_blocked_run": (_i, [_vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp]),
+            "ttm_blocked_destroy": (None, [_vp]),
             "ttm_blocked_peaks": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _d, _vp, _vp,
                                        C.POINTER(_i), _vp]),
             "ttm_mlp_num_params": (_i64, [_i]),
@@ -108,6 +113,7 @@ def lib():
             "ttm_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i64, _vp, C.POINTER(_d), _vp]),
             "ttm_mlp_train": (_i, [_vp, _vp, _vp, _i64, _i, _i, C.c_float, C.c_uint64, C.POINTER(_d), _vp]),
             "ttm_mlp_infer": (_i, [_vp, _vp, _i64, _vp, _vp]),
+            "ttm_mlp_set_precision": (_i, [_vp, _i]),
             "ttm_mlp_make_pairs": (_i, [_vp, _vp, _i, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
             "ttm_mlp_save": (_i, [_vp, C.c_char_p]),
             "ttm_mlp_load": (_i, [_vp, C.c_char_p, C.POINTER(_vp)]),
@@ -349,6 +355,10 @@ class Mlp:
         self.ctx.check(lib().ttm_mlp_forward(self.h, _dev(d_X, torch.float32, "d_X"), d_X.shape[0],
                                              _dev(d_U, torch.float32, "d_U"), _stream(stream)))
 
+    def set_precision(self, mode: int):
+        """TTM_MLP_FP32 (default) or TTM_MLP_BF16 products in forward, loss_grad and train."""
+        self.ctx.check(lib().ttm_mlp_set_precision(self.h, int(mode)))
+
     def infer(self, d_X, d_U, stream=None):
         import torch
         self.ctx.check(lib().ttm_mlp_infer(self.h, _dev(d_X, torch.float32, "d_X"), d_X.shape[0],
@@ -523,6 +533,45 @@ def ttm_blocked_peaks(ctx: Context, d_field, p: ttm_field_params, tomo, slab_z: 
                                       float(min_dist), idx.ctypes.data, val.ctypes.data, C.byref(n),
                                       _stream(stream)))
     return idx[:n.value], val[:n.value]
+
+
+class Blocked:
+    """ttm_blocked: block processing (Sec. 3.4) kept across tomograms of one shape."""
+
+    def __init__(self, ctx: Context, d_field, p: ttm_field_params, shape, slab_z: int):
+        import torch
+        K, tz, ty, tx = d_field.shape
+        Z, Y, X = shape
+        h = _vp()
+        ctx.check(lib().ttm_blocked_create(ctx.h, _dev(d_field, torch.float64, "d_field"), tz, ty, tx, C.byref(p),
+                                           Z, Y, X, int(slab_z), C.byref(h)))
+        self.h, self.ctx, self.shape = h, ctx, (Z, Y, X)
+
+    def run(self, tomo, P: int, min_dist: float, map_kind: int = 0, stream=None):
+        """tomo: float32 host array (numpy, or a pinned CPU tensor for
+        copies that overlap the kernels)."""
+        if hasattr(tomo, "data_ptr"):
+            if tuple(tomo.shape) != self.shape or not tomo.is_contiguous():
+                raise ValueError("tomogram shape or layout differs from the session's")
+            ptr = tomo.data_ptr()
+        else:
+            tomo = np.ascontiguousarray(tomo, dtype=np.float32)
+            if tomo.shape != self.shape:
+                raise ValueError("tomogram shape differs from the session's")
+            ptr = tomo.ctypes.data
+        idx = np.zeros(max(P, 1), dtype=np.int64)
+        val = np.zeros(max(P, 1), dtype=np.float32)
+        n = C.c_int(0)
+        self.ctx.check(lib().ttm_blocked_run(self.h, ptr, int(map_kind), int(P), float(min_dist), idx.ctypes.data,
+                                             val.ctypes.data, C.byref(n), _stream(stream)))
+        return idx[:n.value], val[:n.value]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ttm_blocked_destroy(self.h)
+            self.h = None
+
+    __del__ = close
 
 
 def ttm_find_peaks_noalloc(ctx: Context, d_map, box, P: int, min_dist: float, stream=None):

@@ -80,3 +80,26 @@ def test_blocked_peaks_rejects_bad_arguments(T, ctx):
         T.ttm_blocked_peaks(ctx, field, p, vol, 0, 5, 4.0)
     with pytest.raises(T.TTMError):
         T.ttm_blocked_peaks(ctx, field, p, vol[:5], 4, 5, 4.0)
+
+
+def test_blocked_session_reused_and_equal_to_one_shot(T, ctx):
+    """A block-processing session kept across tomograms (plans, buffers and
+    the copy stream made once): two different tomograms run through one
+    session give the one-shot call's lists, also from pinned host memory."""
+    shape = (70, 48, 56)
+    N, r, n = 12, 5.0, 4
+    tmpl = synth.gaussian_blob_template(N, seed=43).astype(np.float32)
+    p = T.params(order_n=n, mask_radius=r, n_rot_base=32)
+    K = T.ttm_num_components(n)
+    field = torch.empty((K, N, N, N), dtype=torch.float64, device="cuda")
+    T.ttm_build_tensor_field(ctx, dev(tmpl), p, field)
+    sess = T.Blocked(ctx, field, p, shape, 24)
+    for seed in (44, 45):
+        vol, _ = synth.make_tomogram(shape, tmpl, r, 6, seed=seed, amplitude=1.0)
+        oi, ov = T.ttm_blocked_peaks(ctx, field, p, vol, 24, 30, 2 * r)
+        si, sv = sess.run(vol, 30, 2 * r)
+        pi, pv = sess.run(torch.as_tensor(vol).pin_memory(), 30, 2 * r)
+        assert list(si) == list(oi) and list(pi) == list(oi) and len(oi) > 10
+        assert np.array_equal(sv, ov) and np.array_equal(pv, ov)
+    with pytest.raises(ValueError):
+        sess.run(np.zeros((10, 10, 10), np.float32), 5, 1.0)

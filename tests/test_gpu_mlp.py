@@ -72,6 +72,30 @@ def test_mlp_gradient_matches_oracle(T, net_and_data):
     assert np.abs(g.cpu().numpy() - go).max() <= 1e-4 * np.abs(go).max()
 
 
+def test_mlp_bf16_training_gradient_close_to_oracle(T, ctx, net_and_data):
+    """TTM_MLP_BF16: the forward and backward products take BF16 operands on
+    the tensor cores (FP32 accumulation). Loss and gradient against the
+    oracle's FP64 ones on identical weights, within what BF16 rounding of
+    the operands (unit roundoff 2^-8, three layers) allows; the gradient
+    direction is kept (cosine > 0.999)."""
+    m0, p, X, U = net_and_data
+    m = T.Mlp(ctx, m0.K, seed=1)
+    m.set_params(m0.get_params())
+    m.set_precision(T.TTM_MLP_BF16)
+    _, Lo, go = O.mlp(p, X.astype(np.float64), U.astype(np.float64), want_grad=True)
+    g = torch.zeros(m.num_params, device="cuda")
+    L = m.loss_grad(dev(X), dev(U), g)
+    gb = g.cpu().numpy().astype(np.float64)
+    assert abs(L - Lo) <= 1e-2 * Lo
+    assert np.abs(gb - go).max() <= 5e-2 * np.abs(go).max()
+    assert gb @ go / (np.linalg.norm(gb) * np.linalg.norm(go)) > 0.999
+    m.set_precision(T.TTM_MLP_FP32)
+    L32 = m.loss_grad(dev(X), dev(U), g)
+    assert abs(L32 - Lo) <= 1e-6 * Lo
+    with pytest.raises(T.TTMError):
+        m.set_precision(2)
+
+
 def test_mlp_bf16_inference_close_to_oracle(T, net_and_data):
     """Tensor-core inference (BF16 operands, FP32 accumulation, tanh.approx
     GELU): direction within a BF16 tolerance of the FP64 forward."""
@@ -125,6 +149,15 @@ def trained(T, ctx):
     for ep in range(10):
         net.train(dX, dU, epochs=1, batch=4096, lr=3e-4, seed=200 + ep)
     loss1 = net.loss_grad(dX, dU, g) / idx.size
+    # the same schedule in BF16 (tensor-core products, FP32 master weights)
+    net16 = T.Mlp(ctx, K, seed=5)
+    net16.set_precision(T.TTM_MLP_BF16)
+    for ep in range(20):
+        net16.train(dX, dU, epochs=1, batch=4096, lr=1e-3, seed=100 + ep)
+    for ep in range(10):
+        net16.train(dX, dU, epochs=1, batch=4096, lr=3e-4, seed=200 + ep)
+    net16.set_precision(T.TTM_MLP_FP32)
+    loss1_bf16 = net16.loss_grad(dX, dU, g) / idx.size
     # held-out tomogram, plain and learned maps
     vol2, planted = synth.make_tomogram(shape, tmpl, R, 30, 12, snr=0.1, lowpass=True)
     M.run(dev(vol2))
@@ -134,12 +167,28 @@ def trained(T, ctx):
     T.ttm_peak_map(M.plan, M.C, sl, ol, fl, mlp=net)
     torch.cuda.synchronize()
     fb = T.ttm_plan_fallback_count(M.plan)
+    sl16 = torch.empty_like(M.score)
+    ol16 = torch.empty_like(M.orient)
+    T.ttm_peak_map(M.plan, M.C, sl16, ol16, mlp=net16)
+    torch.cuda.synchronize()
     return dict(tmpl=tmpl, p=p, M=M, net=net, loss0=loss0, loss1=loss1, sl=sl, ol=ol, fl=fl, fb=fb, box=b,
-                centres=planted.centres, vol2=vol2)
+                centres=planted.centres, vol2=vol2, net16=net16, loss1_bf16=loss1_bf16, sl16=sl16)
 
 
 def test_training_reduces_loss(trained):
     assert trained["loss1"] < 0.6 * trained["loss0"]
+
+
+def test_bf16_training_matches_fp32_training(trained):
+    """BF16 training (the same initial weights, pairs and schedule) reaches
+    the loss of FP32 training to within 10 %, and the learned maximiser with
+    the BF16-trained network is also never more than 1e-4 below the plain
+    one over every valid voxel."""
+    assert trained["loss1_bf16"] < 0.6 * trained["loss0"]
+    assert trained["loss1_bf16"] <= 1.1 * trained["loss1"] + 1e-3, (trained["loss1_bf16"], trained["loss1"])
+    M, b = trained["M"], trained["box"]
+    d = (trained["sl16"] - M.score)[b[0]:b[1], b[2]:b[3], b[4]:b[5]]
+    assert int((d < -S_TOL).sum()) == 0
 
 
 def test_learned_never_below_plain(trained):
