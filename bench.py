@@ -39,6 +39,39 @@ METRIC = "TTM voxels/s (score+orientation map)"
 UNIT = "voxels/s"
 
 
+def kernel_sources_digest() -> str:
+    """SHA-256 over the CUDA sources of the library (file names and bytes,
+    sorted), to tell whether a recorded ncu figure still describes them."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2408_02398_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(name: str):
+    """DRAM bytes per voxel of one ttm_correlate call (all its kernels), from
+    an ncu summary under profiles/ that states `dram_bytes_per_voxel:` and the
+    `sources_sha256:` of the kernels it measured; None when the kernels have
+    changed since."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        line = line.strip().strip("`")
+        for key in ("dram_bytes_per_voxel:", "sources_sha256:"):
+            if line.startswith(key):
+                vals[key] = line[len(key):].strip()
+    if vals.get("sources_sha256:") != kernel_sources_digest() or "dram_bytes_per_voxel:" not in vals:
+        return None
+    return float(vals["dram_bytes_per_voxel:"])
+
+
 def peaks_file():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -521,9 +554,12 @@ def run_ours(args, ws, rank, local):
                "note": "issue-bound on the scalar Newton / start work around the probe product"}
     roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
+    tpv = recorded_traffic("traffic_correlate_n4.md")
     roof_corr = {"bound": "hbm", "kernel": "ttm_correlate (stages prefilter..xpass)",
                  "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                 "peak_source": how, "traffic": None, "bytes_per_voxel": 4 + 4 * K}
+                 "peak_source": how, "traffic": None if tpv is None else tpv * V, "bytes_per_voxel": 4 + 4 * K,
+                 "traffic_source": "profiles/traffic_correlate_n4.md (ncu dram bytes of every ttm_correlate kernel "
+                                   "on 128x512x512, per voxel, scaled; null once the kernels changed)"}
     roof_corr["frac"] = roof_corr["achieved"] / roof_corr["peak"]
     dominant = roof_pm if st_ms["peak_map"] >= corr_ms else roof_corr
     other_roof = roof_corr if dominant is roof_pm else roof_pm

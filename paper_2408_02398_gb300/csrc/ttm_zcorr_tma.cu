@@ -81,6 +81,10 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
     const int64_t c = c0 + w;
     const bool act = c < ncols;
     const uint32_t sbytes = (uint32_t)(tzn * W * sizeof(TS));
+    // box x coordinates in 32-bit elements: two per FP32 complex value, one
+    // per 16-bit pair
+    const int xg = (int)(2 * c0);
+    const int xs = (int)(c0 * (int64_t)(sizeof(TS) / 4));
     if (t == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -90,9 +94,9 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
     __syncthreads();
     if (t == 0) {
         mbar_expect_tx(&bars[0], (uint32_t)(Z * W * sizeof(float2)));
-        tma_load_2d(gt, &tmG, (int)(2 * c0), 0, &bars[0]);
+        tma_load_2d(gt, &tmG, xg, 0, &bars[0]);
         mbar_expect_tx(&bars[1], sbytes);
-        tma_load_2d(sbuf[0], &tmS, (int)(2 * c0), 0, &bars[1]);
+        tma_load_2d(sbuf[0], &tmS, xs, 0, &bars[1]);
     }
     fs_load_tw<float>(tw, twg, Z);
     // a wait that expired: record it, let the copies in flight land (each
@@ -112,7 +116,7 @@ k_zcorr_tma(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUt
         if (t == 0 && a + 1 < K) {
             // the other buffer held component a - 1, read before the last barrier
             mbar_expect_tx(&bars[1 + (buf ^ 1)], sbytes);
-            tma_load_2d(sbuf[buf ^ 1], &tmS, (int)(2 * c0), (a + 1) * tzn, &bars[1 + (buf ^ 1)]);
+            tma_load_2d(sbuf[buf ^ 1], &tmS, xs, (a + 1) * tzn, &bars[1 + (buf ^ 1)]);
         }
         if (__syncthreads_or(!mbar_wait(&bars[1 + buf], (a >> 1) & 1, wait_limit))) {
             if (t == 0) atomicExch(err, 1);
