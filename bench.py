@@ -400,9 +400,18 @@ def forms_order4(ttm, ctx, wl, dev, steps, warmup, crop_voxels):
         ttm.ttm_plan_set_localsum(plan, ttm.TTM_LOCALSUM_DF64)
         mc = _step_ms(lambda: ttm.ttm_correlate(plan, d_tomo, C), steps, warmup, stream)
         mp = _step_ms(lambda: ttm.ttm_peak_map(plan, C, score, orient), steps, warmup, stream)
+        # per-stage times of separate, instrumented calls (not the timed ones)
+        ttm.ttm_plan_stage_times(plan)
+        ttm.ttm_plan_enable_timing(plan, True)
+        for _ in range(steps):
+            ttm.ttm_correlate(plan, d_tomo, C)
+            ttm.ttm_peak_map(plan, C, score, orient)
+        st = {k: v / steps for k, v in ttm.ttm_plan_stage_times(plan).items()}
+        ttm.ttm_plan_enable_timing(plan, False)
         got = C.reshape(K, -1)[:, tv].cpu().numpy().astype(np.float64)
         sg = score.flatten()[tv].cpu().numpy().astype(np.float64)
         out[name] = {"correlate_ms": mc, "peak_map_ms": mp, "voxels_per_s": V / ((mc + mp) / 1e3),
+                     "stages_ms": st,
                      "C_max_abs_err": float(np.abs(got - Cref).max()),
                      "C_rel_l2_err": float(np.linalg.norm(got - Cref) / np.linalg.norm(Cref)),
                      "score_max_abs_err": float(np.abs(sg - sref).max())}
