@@ -76,7 +76,9 @@ __device__ __forceinline__ df64 ddiv(df64 a, df64 b)
     return fast_two_sum(q1, q2);
 }
 
-struct dcx {
+// 16-byte aligned so that an element moves with one vector access (as
+// double2 does) rather than four 4-byte ones
+struct __align__(16) dcx {
     df64 x, y;
 };
 

@@ -255,6 +255,29 @@ __device__ __forceinline__ void load_twiddles(cx<R>* tws, const LenPlan& pl)
     for (int i = threadIdx.x; i < pl.L; i += blockDim.x) tws[i] = g[i];
 }
 
+// Stages n tile elements into shared memory with kLoadBatch global loads
+// per thread issued before any of their shared-memory stores, so that a
+// thread has that many loads in flight instead of waiting on each in turn:
+// get(idx) loads element idx, put(idx, v) stores it into the tile.
+constexpr int kLoadBatch = 8;
+template <typename T, class Get, class Put>
+__device__ __forceinline__ void stage_tile(int n, Get get, Put put)
+{
+    for (int base = threadIdx.x; base < n; base += kLoadBatch * blockDim.x) {
+        T v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; u++) {
+            const int idx = base + u * (int)blockDim.x;
+            if (idx < n) v[u] = get(idx);
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; u++) {
+            const int idx = base + u * (int)blockDim.x;
+            if (idx < n) put(idx, v[u]);
+        }
+    }
+}
+
 // ------------------------------------------------------------ functors --
 
 template <typename R> struct ProIdentity {
@@ -283,7 +306,7 @@ template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
 __global__ void __launch_bounds__(256) k_fft_strided(const In* __restrict__ in, StridedAxis ax, LenPlan pl,
                                                      int W, int ld, Pro pro, Store store)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* bufb = bufa + W * ld;
     cx<R>* tws = bufb + W * ld;
@@ -292,13 +315,17 @@ __global__ void __launch_bounds__(256) k_fft_strided(const In* __restrict__ in, 
     const int64_t i0 = (blockIdx.x - o * tiles_per_outer) * W;
     const int L = pl.L;
     load_twiddles<R>(tws, pl);
-    for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
-        int j = idx / W, w = idx - j * W;
-        int64_t i = i0 + w;
-        cx<R> v = mk<R>(0, 0);
-        if (i < ax.inner) v = pro(load_cx(in[o * ax.os + i + (int64_t)j * ax.s]), o, i, j);
-        bufa[w * ld + j] = v;
-    }
+    stage_tile<cx<R>>(
+        W * L,
+        [&](int idx) {
+            const int j = idx / W, w = idx - j * W;
+            const int64_t i = i0 + w;
+            return i < ax.inner ? pro(load_cx(in[o * ax.os + i + (int64_t)j * ax.s]), o, i, j) : mk<R>(0, 0);
+        },
+        [&](int idx, cx<R> v) {
+            const int j = idx / W, w = idx - j * W;
+            bufa[w * ld + j] = v;
+        });
     __syncthreads();
     cx<R>* res = smem_fft<DIR, R>(bufa, bufb, ld, W, pl, tws);
     for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
@@ -314,20 +341,24 @@ template <typename R, int DIR, class Pro, class Store>
 __global__ void __launch_bounds__(256) k_fft_contig(const cx<R>* __restrict__ in, int64_t nlines, LenPlan pl,
                                                     int W, int ld, Pro pro, Store store)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* bufb = bufa + W * ld;
     cx<R>* tws = bufb + W * ld;
     const int64_t l0 = (int64_t)blockIdx.x * W;
     const int L = pl.L;
     load_twiddles<R>(tws, pl);
-    for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
-        int w = idx / L, j = idx - w * L;
-        int64_t l = l0 + w;
-        cx<R> v = mk<R>(0, 0);
-        if (l < nlines) v = pro(in[l * L + j], l, 0, j);
-        bufa[w * ld + j] = v;
-    }
+    stage_tile<cx<R>>(
+        W * L,
+        [&](int idx) {
+            const int w = idx / L, j = idx - w * L;
+            const int64_t l = l0 + w;
+            return l < nlines ? pro(in[l * L + j], l, 0, j) : mk<R>(0, 0);
+        },
+        [&](int idx, cx<R> v) {
+            const int w = idx / L, j = idx - w * L;
+            bufa[w * ld + j] = v;
+        });
     __syncthreads();
     cx<R>* res = smem_fft<DIR, R>(bufa, bufb, ld, W, pl, tws);
     for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
@@ -345,7 +376,7 @@ template <typename R, class Src>
 __global__ void __launch_bounds__(256) k_r2c_rows(Src src, int64_t nrows, cx<R>* __restrict__ out, LenPlan pl,
                                                   int W, int ld)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* bufb = bufa + W * ld;
     cx<R>* tws = bufb + W * ld;
@@ -386,7 +417,7 @@ template <typename R, class Sink, typename In = cx<R>>
 __global__ void __launch_bounds__(256) k_c2r_rows(const In* __restrict__ in, int64_t nrows, Sink sink,
                                                   LenPlan pl, int W, int ld, int nbatch)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* bufb = bufa + W * ld;
     cx<R>* tws = bufb + W * ld;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(FsThreads<R>::value)
 k_fs_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro pro, Store store)
 {
     using S = FsShape<R, E, P>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* xa = tw + S::L;
     const int t = threadIdx.x;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(FsThreads<R>::value)
 k_fs_contig(const cx<R>* __restrict__ in, int64_t nlines, const void* twg, Pro pro, Store store)
 {
     using S = FsShape<R, E, P>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* xa = tw + S::L;
     const int t = threadIdx.x;
@@ -209,7 +209,7 @@ k_fs_r2c(Src src, int64_t nrows, cx<R>* __restrict__ out, const void* twg)
 {
     using S = FsShape<R, E, P>;
     constexpr int X = S::L, Xh = X / 2 + 1;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* xa = tw + S::L;
     const int t = threadIdx.x;
@@ -261,7 +261,7 @@ k_fs_c2r(const In* __restrict__ in, int64_t nrows, Sink sink, const void* twg, i
 {
     using S = FsShape<R, E, P>;
     constexpr int X = S::L, Xh = X / 2 + 1;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* xa = tw + S::L;
     const int t = threadIdx.x;
@@ -318,7 +318,7 @@ k_fs_zcorr(const float2* __restrict__ G, const TS* __restrict__ spec, int K, int
     using S = FsShape<float, E, P>;
     constexpr int Z = S::L;
     constexpr int ZG = Z | 1;  // odd row stride of the image-spectrum tile
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* xa = tw + S::L;
     const int t = threadIdx.x;

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256)
 k_zcorr(const float2* __restrict__ G, const TS* __restrict__ spec, int K, int tzn, int cz, int64_t ncols,
         TW* __restrict__ out, LenPlan pl, int W, int ld, const float* __restrict__ gmax, float oscale)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* gs = reinterpret_cast<float2*>(smem_raw);
     float2* bufa = gs + W * ld;
     float2* bufb = bufa + W * ld;

@@ -261,18 +261,24 @@ template <typename R, class Mask>
 __global__ void __launch_bounds__(256)
 k_zmask(cx<R>* __restrict__ zd, int64_t ncols, LenPlan pl, int W, int ld, Mask mask)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* bufa = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* bufb = bufa + W * ld;
     cx<R>* tws = bufb + W * ld;
     const int Z = pl.L;
     const int64_t c0 = (int64_t)blockIdx.x * W;
     load_twiddles<R>(tws, pl);
-    for (int idx = threadIdx.x; idx < W * Z; idx += blockDim.x) {
-        const int z = idx / W, w = idx - z * W;
-        const int64_t c = c0 + w;
-        bufa[w * ld + z] = c < ncols ? zd[(int64_t)z * ncols + c] : mk<R>(0, 0);
-    }
+    stage_tile<cx<R>>(
+        W * Z,
+        [&](int idx) {
+            const int z = idx / W, w = idx - z * W;
+            const int64_t c = c0 + w;
+            return c < ncols ? zd[(int64_t)z * ncols + c] : mk<R>(0, 0);
+        },
+        [&](int idx, cx<R> v) {
+            const int z = idx / W, w = idx - z * W;
+            bufa[w * ld + z] = v;
+        });
     __syncthreads();
     cx<R>* p = smem_fft<-1, R>(bufa, bufb, ld, W, pl, tws);
     cx<R>* q = (p == bufa) ? bufb : bufa;
