@@ -15,7 +15,10 @@
 // length-L table exp(-2 pi i t / L) held in shared memory.
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
+#include "fft_cube.cuh"
 
 namespace ttm {
 
@@ -415,6 +418,13 @@ template <typename R, int DIR, class Pro, class Store, typename In = cx<R>>
 inline void launch_strided_any(const In* in, StridedAxis ax, const LenPlan& pl, Pro pro, Store store,
                                cudaStream_t st)
 {
+    if constexpr (std::is_same<R, df64>::value) {
+        if (!pl.no_reg && cube_length(pl.L)) {
+            launch_cube_strided<DIR>(in, ax, pl, pro, store, st);
+            TTM_LAUNCH_CHECK();
+            return;
+        }
+    }
     int E, P;
     if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_strided<R, DIR>(in, ax, pl, pro, store, st); return; }
 #define TTM_L(E_, P_)                                                                          \
@@ -435,6 +445,13 @@ template <typename R, int DIR, class Pro, class Store>
 inline void launch_contig_any(const cx<R>* in, int64_t nlines, const LenPlan& pl, Pro pro, Store store,
                               cudaStream_t st)
 {
+    if constexpr (std::is_same<R, df64>::value) {
+        if (!pl.no_reg && cube_length(pl.L)) {
+            launch_cube_contig<DIR>(in, nlines, pl, pro, store, st);
+            TTM_LAUNCH_CHECK();
+            return;
+        }
+    }
     int E, P;
     if (pl.no_reg || !fs_split(pl.L, E, P)) { launch_contig<R, DIR>(in, nlines, pl, pro, store, st); return; }
 #define TTM_L(E_, P_)                                                                          \

@@ -132,10 +132,11 @@ def test_correlate_periodic_all_voxels(T, ctx, shape, N, r, n, localsum):
 
 
 REG_CASES = [
-    # lengths with register-resident FFT kernels (64, 128, 200, 256) on every axis
+    # lengths with register-resident FFT kernels (64, 128, 200, 256, 512) on every axis
     ((200, 64, 128), 9, 4.0, 4),
     ((64, 256, 64), 8, 3.0, 2),
     ((128, 128, 256), 11, 5.0, 6),
+    ((12, 512, 512), 9, 4.0, 2),
 ]
 
 
@@ -160,6 +161,28 @@ def test_correlate_register_lengths(T, ctx, shape, N, r, n, localsum):
     assert np.abs(got - Cref).max() <= C_TOL * max(1.0, np.abs(Cref).max())
     s, _, _ = O.maximise(Cref, n, 3, nsamples=20000)
     assert np.abs(d_s.cpu().numpy().ravel()[vox] - s).max() <= S_TOL
+
+
+@pytest.mark.parametrize("localsum", LOCALSUMS)
+def test_local_sums_with_cancellation(T, ctx, localsum):
+    """Local sums on 512-point x and y axes for a tomogram 50 + unit noise.
+    The filter keeps the offset and leaves a noise variance of about 0.085,
+    so S2 - S1^2/M cancels about four and a half digits of S2: FP32 local
+    sums would miss w by ~1e-3, the FP64 and double-float ones must still
+    match the oracle's w to the FP32 tolerance at sampled voxels."""
+    shape = (12, 512, 512)
+    V = int(np.prod(shape))
+    tomo = (50.0 + synth.normals(21, 1, V)).reshape(shape).astype(np.float32)
+    tmpl = synth.gaussian_blob_template(9, seed=4)
+    field = oracle_field(tmpl, 4.0, 2, 4)
+    p = T.params(order_n=2, mask_radius=4.0, n_rot_base=4)
+    plan, d_C, d_w, d_s, d_u, d_F = run_gpu(T, ctx, tomo, field, p, localsum)
+    vox = np.sort(np.random.default_rng(5).choice(V, size=1500, replace=False))
+    pr = O.Prepared(tomo.astype(np.float64), tmpl, 4.0)
+    w, S1, S2 = O.local_w(pr.g, pr.m, vox, periodic=True, floor=pr.floor)
+    # the cancellation the case is built for
+    assert np.min((S2 - S1 ** 2 / pr.M) / S2) < 1e-4
+    assert np.abs(d_w.cpu().numpy().ravel()[vox] - w).max() <= W_TOL * np.abs(w).max()
 
 
 @pytest.mark.parametrize("n", [2, 4, 6])
