@@ -18,7 +18,7 @@
 #include <type_traits>
 
 #include "fft.cuh"
-#include "fft_cube.cuh"
+#include "fft_line3.cuh"
 
 namespace ttm {
 
@@ -419,8 +419,8 @@ inline void launch_strided_any(const In* in, StridedAxis ax, const LenPlan& pl, 
                                cudaStream_t st)
 {
     if constexpr (std::is_same<R, df64>::value) {
-        if (!pl.no_reg && cube_length(pl.L)) {
-            launch_cube_strided<DIR>(in, ax, pl, pro, store, st);
+        if (!pl.no_reg && line3_length(pl.L)) {
+            launch_line3_strided<DIR>(in, ax, pl, pro, store, st);
             TTM_LAUNCH_CHECK();
             return;
         }
@@ -446,8 +446,8 @@ inline void launch_contig_any(const cx<R>* in, int64_t nlines, const LenPlan& pl
                               cudaStream_t st)
 {
     if constexpr (std::is_same<R, df64>::value) {
-        if (!pl.no_reg && cube_length(pl.L)) {
-            launch_cube_contig<DIR>(in, nlines, pl, pro, store, st);
+        if (!pl.no_reg && line3_length(pl.L)) {
+            launch_line3_contig<DIR>(in, nlines, pl, pro, store, st);
             TTM_LAUNCH_CHECK();
             return;
         }

@@ -299,6 +299,13 @@ k_zmask(cx<R>* __restrict__ zd, int64_t ncols, LenPlan pl, int W, int ld, Mask m
 template <typename R, class Mask>
 static void launch_zmask(cx<R>* zd, int64_t ncols, const LenPlan& pz, Mask mask, cudaStream_t st)
 {
+    if constexpr (std::is_same<R, df64>::value) {
+        if (!pz.no_reg && line3_length(pz.L)) {
+            launch_line3_zmask(zd, ncols, pz, mask, st);
+            TTM_LAUNCH_CHECK();
+            return;
+        }
+    }
     const int Z = pz.L;
     const int ld = Z | 1;
     int W = 16;
