@@ -130,7 +130,13 @@ const TuneRec& tune_length_df(ttm_ctx* ctx, int L)
     rec.nst = base.nst;
     std::copy(base.rad, base.rad + base.nst, rec.rad);
     int E, P;
-    if (fs_split(L, E, P)) {
+    if (line3_length(L)) {
+        // the three-level register kernel: twice as fast as the shared-memory
+        // pass at 512 and 200, so no timing (which also keeps the choice
+        // the same under a profiler, whose per-launch overhead evens out the
+        // two timings)
+        rec.reg = 1;
+    } else if (fs_split(L, E, P)) {
         const int lines = tune_lines_df(L);
         DevBuf buf;
         buf.alloc((size_t)L * lines * sizeof(dcx));
