@@ -39,35 +39,52 @@ METRIC = "TTM voxels/s (score+orientation map)"
 UNIT = "voxels/s"
 
 
-def kernel_sources_digest() -> str:
-    """SHA-256 over the CUDA sources of the library (file names and bytes,
-    sorted), to tell whether a recorded ncu figure still describes them."""
+def kernel_sources_digest(entry: str = "") -> str:
+    """SHA-256 over CUDA sources of the library (file names and bytes,
+    sorted), to tell whether a recorded ncu figure still describes them: all
+    of csrc/, or with `entry` (a csrc/ file name) that file and the headers
+    it includes, directly or not."""
     import glob
     import hashlib
-    h = hashlib.sha256()
+    import re
     csrc = os.path.join(ROOT, "paper_2408_02398_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
-                    glob.glob(os.path.join(csrc, "*.h"))):
+    if entry:
+        files, todo = set(), [os.path.join(csrc, entry)]
+        while todo:
+            f = os.path.normpath(todo.pop())
+            if f in files or not os.path.exists(f):
+                continue
+            files.add(f)
+            for inc in re.findall(r'^\s*#include\s+"([^"]+)"', open(f).read(), re.M):
+                todo.append(os.path.join(os.path.dirname(f), inc))
+        files = sorted(files)
+    else:
+        files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                       glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
         h.update(os.path.basename(f).encode())
         h.update(open(f, "rb").read())
     return h.hexdigest()
 
 
 def recorded_traffic(name: str):
-    """DRAM bytes per voxel of one ttm_correlate call (all its kernels), from
-    an ncu summary under profiles/ that states `dram_bytes_per_voxel:` and the
-    `sources_sha256:` of the kernels it measured; None when the kernels have
-    changed since."""
+    """DRAM bytes per voxel recorded in an ncu summary under profiles/ that
+    states `dram_bytes_per_voxel:`, the `sources_sha256:` of the kernels it
+    measured and, optionally, `sources:` (the csrc/ file those kernels come
+    from, for a digest of that file and its headers only); None when the
+    sources have changed since."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
         line = line.strip().strip("`")
-        for key in ("dram_bytes_per_voxel:", "sources_sha256:"):
+        for key in ("dram_bytes_per_voxel:", "sources_sha256:", "sources:"):
             if line.startswith(key):
                 vals[key] = line[len(key):].strip()
-    if vals.get("sources_sha256:") != kernel_sources_digest() or "dram_bytes_per_voxel:" not in vals:
+    if vals.get("sources_sha256:") != kernel_sources_digest(vals.get("sources:", "")) or \
+            "dram_bytes_per_voxel:" not in vals:
         return None
     return float(vals["dram_bytes_per_voxel:"])
 
@@ -556,10 +573,14 @@ def run_ours(args, ws, rank, local):
     tc_peak = float(pk.get("bf16_tflops", 1900.0))
     kpad = (K + 15) // 16 * 16
     pm_flops = 2.0 * kpad * 128 * V
+    tpm = recorded_traffic("traffic_peakmap_n4.md") if n == 4 else None
     roof_pm = {"bound": "tensor", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
                "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
                "peak_source": how + " dense BF16 (burst); FP16 mma has the same rate",
-               "traffic": None, "flops_per_voxel": 2 * kpad * 128,
+               "traffic": None if tpm is None else tpm * V,
+               "traffic_source": "profiles/traffic_peakmap_n4.md (ncu dram bytes of one k_peakmap<4> launch on "
+                                 "200x256x256, per voxel, scaled to this launch; null once its sources changed)",
+               "flops_per_voxel": 2 * kpad * 128,
                "note": "issue-bound on the scalar Newton / start work around the probe product"}
     roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
@@ -568,7 +589,8 @@ def run_ours(args, ws, rank, local):
                  "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                  "peak_source": how, "traffic": None if tpv is None else tpv * V, "bytes_per_voxel": 4 + 4 * K,
                  "traffic_source": "profiles/traffic_correlate_n4.md (ncu dram bytes of every ttm_correlate kernel "
-                                   "on 128x512x512, per voxel, scaled; null once the kernels changed)"}
+                                   "on 200x512x512 sizes of each pass, per voxel, scaled; null once the kernels "
+                                   "changed)"}
     roof_corr["frac"] = roof_corr["achieved"] / roof_corr["peak"]
     dominant = roof_pm if st_ms["peak_map"] >= corr_ms else roof_corr
     other_roof = roof_corr if dominant is roof_pm else roof_pm

@@ -180,7 +180,7 @@ k_line3_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro 
 // forward transform along z (R1 R2 R3), the product with the mask spectrum
 // (mask(v, 0, column, kz)) and the inverse transform (R3 R2 R1), in place.
 template <int R1, int R2, int R3, int NL, class Mask>
-__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T)
+__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T, 65536 / (NL * Line3<R1, R2, R3>::T * 64))
 k_line3_zmask(dcx* __restrict__ zd, int64_t ncols, const void* twg, Mask mask)
 {
     using F = Line3<R1, R2, R3>;
