@@ -560,8 +560,8 @@ def run_ours(args, ws, rank, local):
 
     # Rooflines (stages: per-step milliseconds of CUDA events on the
     # launching stream). The maximiser's dense work is the probe product on
-    # the tensor cores (FP16 mma.sync, same rate as BF16): 2 K_pad P flops
-    # per voxel (K padded to a multiple of 16, P = 128 probes), against the
+    # the tensor cores (FP16 mma.sync, same rate as BF16): 2 K P flops per
+    # voxel (P = 128 probes; the kernel pads K to 16, which is not counted), against the
     # measured dense 16-bit peak; its time goes to the scalar Newton and
     # start-selection work around that product (instruction issue), so the
     # fraction is small by construction. The correlate path is HBM-bound:
@@ -571,8 +571,7 @@ def run_ours(args, ws, rank, local):
     pk, how = peaks_file()
     hbm = float(pk.get("hbm_gbs", 6800.0))
     tc_peak = float(pk.get("bf16_tflops", 1900.0))
-    kpad = (K + 15) // 16 * 16
-    pm_flops = 2.0 * kpad * 128 * V
+    pm_flops = 2.0 * K * 128 * V
     tpm = recorded_traffic("traffic_peakmap_n4.md") if n == 4 else None
     roof_pm = {"bound": "tensor", "kernel": "k_peakmap<%d> (ttm_peak_map)" % n,
                "achieved": pm_flops / (st_ms["peak_map"] / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
@@ -580,7 +579,7 @@ def run_ours(args, ws, rank, local):
                "traffic": None if tpm is None else tpm * V,
                "traffic_source": "profiles/traffic_peakmap_n4.md (ncu dram bytes of one k_peakmap<4> launch on "
                                  "200x256x256, per voxel, scaled to this launch; null once its sources changed)",
-               "flops_per_voxel": 2 * kpad * 128,
+               "flops_per_voxel": 2 * K * 128,
                "note": "issue-bound on the scalar Newton / start work around the probe product"}
     roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
