@@ -68,6 +68,23 @@ def kernel_sources_digest(entry: str = "") -> str:
     return h.hexdigest()
 
 
+def recorded_value(name: str, key: str):
+    """A figure `key:` recorded in an ncu summary under profiles/, with the
+    same source-digest check as recorded_traffic; None when absent or stale."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        line = line.strip().strip("`")
+        for k in (key + ":", "sources_sha256:", "sources:"):
+            if line.startswith(k):
+                vals[k] = line[len(k):].strip()
+    if vals.get("sources_sha256:") != kernel_sources_digest(vals.get("sources:", "")) or key + ":" not in vals:
+        return None
+    return float(vals[key + ":"])
+
+
 def recorded_traffic(name: str):
     """DRAM bytes per voxel recorded in an ncu summary under profiles/ that
     states `dram_bytes_per_voxel:`, the `sources_sha256:` of the kernels it
@@ -580,7 +597,9 @@ def run_ours(args, ws, rank, local):
                "traffic_source": "profiles/traffic_peakmap_n4.md (ncu dram bytes of one k_peakmap<4> launch on "
                                  "200x256x256, per voxel, scaled to this launch; null once its sources changed)",
                "flops_per_voxel": 2 * K * 128,
-               "note": "issue-bound on the scalar Newton / start work around the probe product"}
+               "note": "issue-bound on the scalar Newton / start work around the probe product",
+               "warp_inst_per_voxel": recorded_value("k_peakmap_n4_64x512x512.md", "warp_inst_per_voxel") if n == 4
+               else None}
     roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
     alg_bytes_corr = (4 + 4 * K) * V
     tpv = recorded_traffic("traffic_correlate_n4.md")
