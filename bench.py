@@ -607,7 +607,7 @@ def run_ours(args, ws, rank, local):
                  "achieved": alg_bytes_corr / (corr_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                  "peak_source": how, "traffic": None if tpv is None else tpv * V, "bytes_per_voxel": 4 + 4 * K,
                  "traffic_source": "profiles/traffic_correlate_n4.md (ncu dram bytes of every ttm_correlate kernel "
-                                   "on 200x512x512 sizes of each pass, per voxel, scaled; null once the kernels "
+                                   "on 200x256x256, per voxel, scaled to this call; null once the kernels "
                                    "changed)"}
     roof_corr["frac"] = roof_corr["achieved"] / roof_corr["peak"]
     dominant = roof_pm if st_ms["peak_map"] >= corr_ms else roof_corr

@@ -236,7 +236,7 @@ extern "C" ttm_status ttm_blocked_run(ttm_blocked* B, const float* h_tomo, int m
                               stream);
             if (rc != TTM_OK) throw Error{rc, ttm_last_error(ctx)};
             const Prep& p = plan->prep;
-            k_localmax_slab<<<4 * 152 * 8, 256, 0, st>>>(B->d_map.as<float>(), p.Y, p.X, o0 - i0, o1 - i0, m0 - i0,
+            k_localmax_slab<<<32 * B->ctx->num_sms, 256, 0, st>>>(B->d_map.as<float>(), p.Y, p.X, o0 - i0, o1 - i0, m0 - i0,
                                                           m1 - i0, y0, y1, x0, x1, (int64_t)i0, Y, X, B->cap, cidx,
                                                           cval, B->cnt.as<unsigned long long>());
             TTM_LAUNCH_CHECK();

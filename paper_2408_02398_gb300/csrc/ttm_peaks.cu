@@ -51,7 +51,7 @@ int find_peaks_run(ttm_plan* P, const float* d_map, int Pk, double min_dist, int
     float* cval = reinterpret_cast<float*>(cidx + P->cand_cap);
     unsigned long long* cnt = P->cand_count.as<unsigned long long>();
     TTM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-    k_localmax<<<4 * 152 * 8, 256, 0, st>>>(d_map, p.Z, p.Y, p.X, b[0], b[1], b[2], b[3], b[4], b[5], P->cand_cap,
+    k_localmax<<<32 * P->ctx->num_sms, 256, 0, st>>>(d_map, p.Z, p.Y, p.X, b[0], b[1], b[2], b[3], b[4], b[5], P->cand_cap,
                                            cidx, cval, cnt);
     TTM_LAUNCH_CHECK();
     unsigned long long n = 0;
@@ -338,7 +338,7 @@ extern "C" ttm_status ttm_find_peaks_noalloc(ttm_ctx* ctx, const float* d_map, i
         int* ocnt = reinterpret_cast<int*>(s + kOffOutCount);
         // the candidate counter must start at zero on every call
         TTM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-        k_localmax<<<4 * 152 * 8, 256, 0, st>>>(d_map, Z, Y, X, box[0], box[1], box[2], box[3], box[4], box[5],
+        k_localmax<<<32 * ctx->num_sms, 256, 0, st>>>(d_map, Z, Y, X, box[0], box[1], box[2], box[3], box[4], box[5],
                                                kStaticCand, cidx, cval, cnt);
         TTM_LAUNCH_CHECK();
         k_select_greedy<<<1, 1024, 0, st>>>(cnt, kStaticCand, P, min_dist * min_dist, X, Y, cidx, cval, oidx, oval,
