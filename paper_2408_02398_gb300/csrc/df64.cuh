@@ -104,6 +104,39 @@ __device__ __forceinline__ df64 dot2(df64 a, df64 b, df64 c, df64 d)
     return fast_two_sum(s.hi, s.lo + e);
 }
 
+// Addition without the final renormalisation: the head sum is exact
+// (TwoSum) and the tails are summed in FP32, so |lo| may exceed half an ulp
+// of hi by a few ulps. The butterflies of one DFT add with it and
+// renormalise their outputs once (dft in fft.cuh): 8 operations per
+// addition instead of 11. Emulated on 3 000 random radix-8 DFTs the largest
+// error grew from 1.29e-14 to 1.51e-14 of the input norm.
+__device__ __forceinline__ df64 add_lazy(df64 a, df64 b)
+{
+    const df64 s = two_sum(a.hi, b.hi);
+    return df64(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dcx cadd(dcx a, dcx b)
+{
+    dcx r;
+    r.x = add_lazy(a.x, b.x);
+    r.y = add_lazy(a.y, b.y);
+    return r;
+}
+__device__ __forceinline__ dcx csub(dcx a, dcx b)
+{
+    dcx r;
+    r.x = add_lazy(a.x, -b.x);
+    r.y = add_lazy(a.y, -b.y);
+    return r;
+}
+__device__ __forceinline__ dcx renormalise(dcx a)
+{
+    dcx r;
+    r.x = fast_two_sum(a.x.hi, a.x.lo);
+    r.y = fast_two_sum(a.y.hi, a.y.lo);
+    return r;
+}
+
 // the complex product in double-float, one dot2 per component (chosen over
 // the generic cmul by overload resolution)
 __device__ __forceinline__ dcx cmul(dcx a, dcx b)

@@ -14,6 +14,8 @@
 // DIR = +1 the unnormalised inverse.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -187,6 +189,12 @@ template <int RAD, int DIR, typename R> __device__ __forceinline__ void dft(cx<R
     else if constexpr (RAD == 5) dft5<DIR, R>(v);
     else if constexpr (RAD == 7) dft7<DIR, R>(v);
     else dft8<DIR, R>(v);
+    // double-float butterflies add without renormalising (df64.cuh): once
+    // per output here
+    if constexpr (std::is_same<R, df64>::value) {
+#pragma unroll
+        for (int r = 0; r < RAD; r++) v[r] = renormalise(v[r]);
+    }
 }
 
 // ----------------------------------------------------------- stages --
