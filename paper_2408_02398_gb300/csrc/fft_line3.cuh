@@ -141,6 +141,33 @@ k_line3_contig(const dcx* __restrict__ in, int64_t nlines, const void* twg, Pro 
     }
 }
 
+// contiguous lines produced by a source functor: src(l, j) gives element j
+// of line l (so the line can be formed from other data as it is loaded)
+template <int R1, int R2, int R3, int NL, int DIR, class Src, class Store>
+__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T)
+k_line3_contig_src(int64_t nlines, const void* twg, Src src, Store store)
+{
+    using S = Line3<R1, R2, R3>;
+    constexpr int LW = l3_line_stride(S::ROWS, NL);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dcx* tw = reinterpret_cast<dcx*>(smem_raw);
+    dcx* xb = tw + S::NTW;
+    line3_twiddles<R1, R2, R3, DIR>(tw, twg);
+    const int u = threadIdx.x % S::T, w = threadIdx.x / S::T;
+    const int64_t l = (int64_t)blockIdx.x * NL + w;
+    const bool act = l < nlines;
+    dcx x[S::RMAX];
+    if (u < S::P) {
+#pragma unroll
+        for (int m = 0; m < R1; m++) x[m] = act ? src(l, u + S::P * m) : dcx_zero();
+    }
+    line3_run<R1, R2, R3, DIR>(x, u, xb + w * LW, tw);
+    if (act && u < R1 * R2) {
+#pragma unroll
+        for (int t = 0; t < R3; t++) store(x[t], l, 0, u + R1 * R2 * t);
+    }
+}
+
 // strided axis: lines (o, i) with elements o os + i + j s; NL lines adjacent
 // in i per CTA, thread w + NL u works on line i0 + w (w fastest, so a warp
 // reads runs of NL adjacent elements)
@@ -245,6 +272,23 @@ inline void launch_line3_contig(const dcx* in, int64_t nlines, const LenPlan& pl
         const int64_t grid = ceil_div(grid0, (int64_t)NL);                                     \
         TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "contiguous pass grid too large");            \
         k<<<(unsigned)grid, NL * Line3<R1_, R2_, R3_>::T, smem, st>>>(in, nlines, pl.tw, pro, store); \
+    }
+    TTM_LINE3_SWITCH(pl.L, TTM_L3)
+#undef TTM_L3
+}
+
+template <int DIR, class Src, class Store>
+inline void launch_line3_contig_src(int64_t nlines, const LenPlan& pl, Src src, Store store, cudaStream_t st)
+{
+#define TTM_L3(R1_, R2_, R3_)                                                                  \
+    {                                                                                          \
+        constexpr int NL = 4;                                                                  \
+        auto k = k_line3_contig_src<R1_, R2_, R3_, NL, DIR, Src, Store>;                        \
+        constexpr size_t smem = line3_smem<R1_, R2_, R3_, NL>();                               \
+        set_smem(k, smem);                                                                     \
+        const int64_t grid = ceil_div(nlines, (int64_t)NL);                                    \
+        TTM_REQUIRE(grid < (1ll << 31), E_SHAPE, "contiguous pass grid too large");            \
+        k<<<(unsigned)grid, NL * Line3<R1_, R2_, R3_>::T, smem, st>>>(nlines, pl.tw, src, store); \
     }
     TTM_LINE3_SWITCH(pl.L, TTM_L3)
 #undef TTM_L3

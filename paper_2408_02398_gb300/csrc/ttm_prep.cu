@@ -68,6 +68,8 @@ constexpr int kPreThreads = 256;
 // one-voxel spill). Only tomogram voxels enter the g^2 partial sums.
 constexpr int kPreVox = 4;
 
+// DF: the (g, g^2) pack of the local sums in double-float, else in FP64;
+// zc == nullptr: no pack (the first local-sum pass forms it from g32)
 template <bool DF>
 __global__ void __launch_bounds__(kPreThreads)
 k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, int X, float a,
@@ -113,7 +115,8 @@ k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, i
         for (int k = 0; k < kPreVox; k++) {
             if (x0 + k >= X) break;
             g32[v0 + k] = g[k];
-            if (DF) {
+            if (!zc) {
+            } else if (DF) {
                 // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
                 const df64 s2 = two_prod(g[k], g[k]);
                 reinterpret_cast<float4*>(zc)[v0 + k] = make_float4(g[k], 0.f, s2.hi, s2.lo);
@@ -216,6 +219,25 @@ struct StoreW {
         w[l * X + j] = (var > floor[0] && var > 1e-10 * S2) ? (float)(1.0 / sqrt(var)) : 0.0f;
     }
 };
+
+// the (g, g^2) line of the double-float local sums formed from g as it is
+// loaded: g exact in the head, g^2 exact as a TwoProd pair
+struct SrcGSquared {
+    const float* g;
+    int X;
+    __device__ dcx operator()(int64_t l, int j) const
+    {
+        const float v = __ldg(g + l * X + j);
+        dcx r;
+        r.x = df64(v, 0.f);
+        r.y = two_prod(v, v);
+        return r;
+    }
+};
+
+// whether the first double-float local-sum pass reads g itself (a length
+// with the three-level register kernel), so the prefilter writes no pack
+static bool localsum_reads_g(const Prep& p) { return p.localsum_mode == 1 && !p.pxd.no_reg && line3_length(p.X); }
 
 // double-float versions of the mask-spectrum prologue and the w epilogue
 struct ProMaskSpectrumDF {
@@ -386,9 +408,9 @@ void prep_filter(Prep& p, const float* d_tomo, cudaStream_t st)
 {
     const int64_t Vt = (int64_t)p.Zt * p.Yt * p.Xt;
     if (p.localsum_mode == 1)
-        k_prefilter<true><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Zt, p.Yt, p.Xt, p.Z, p.Y, p.X,
-                                                                     (float)p.filter_a, p.g32.as<float>(),
-                                                                     p.zc.as<double2>(), p.partials.as<double>());
+        k_prefilter<true><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(
+            d_tomo, p.Zt, p.Yt, p.Xt, p.Z, p.Y, p.X, (float)p.filter_a, p.g32.as<float>(),
+            localsum_reads_g(p) ? nullptr : p.zc.as<double2>(), p.partials.as<double>());
     else
         k_prefilter<false><<<(unsigned)p.nblk_pre, kPreThreads, 0, st>>>(d_tomo, p.Zt, p.Yt, p.Xt, p.Z, p.Y, p.X,
                                                                       (float)p.filter_a, p.g32.as<float>(),
@@ -419,7 +441,13 @@ void prep_localsums(Prep& p, cudaStream_t st)
     const int64_t YX = (int64_t)Y * X;
     if (p.localsum_mode == 1) {
         dcx* zd = p.zc.as<dcx>();
-        launch_contig_any<df64, -1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(), StoreTo<df64>{zd, X, 1}, st);
+        if (localsum_reads_g(p))
+            launch_line3_contig_src<-1>((int64_t)Z * Y, p.pxd, SrcGSquared{p.g32.as<float>(), X},
+                                        StoreTo<df64>{zd, X, 1}, st);
+        else
+            launch_contig_any<df64, -1>(zd, (int64_t)Z * Y, p.pxd, ProIdentity<df64>(), StoreTo<df64>{zd, X, 1},
+                                        st);
+        TTM_LAUNCH_CHECK();
         launch_strided_any<df64, -1>(zd, StridedAxis{X, Z, YX, X}, p.pyd, ProIdentity<df64>(),
                                      StoreTo<df64>{zd, YX, X}, st);
         launch_zmask<df64>(zd, YX, p.pzd, ProMaskSpectrumDF{p.mhat_df.as<float2>(), Z, Y, X}, st);
