@@ -246,10 +246,12 @@ k_line3_zmask(dcx* __restrict__ zd, int64_t ncols, const void* twg, Mask mask)
 #define TTM_LINE3_SWITCH(L, MACRO)                  \
     switch (L) {                                    \
         case 512: MACRO(8, 8, 8); break;            \
+        case 256: MACRO(8, 8, 4); break;            \
         case 200: MACRO(8, 5, 5); break;            \
+        case 128: MACRO(8, 4, 4); break;            \
         default: throw Error{E_INTERNAL, "no three-level register FFT for this length"}; \
     }
-inline bool line3_length(int L) { return L == 512 || L == 200; }
+inline bool line3_length(int L) { return L == 512 || L == 256 || L == 200 || L == 128; }
 
 template <int R1, int R2, int R3, int NL>
 constexpr size_t line3_smem()

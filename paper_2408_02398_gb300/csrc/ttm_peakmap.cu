@@ -16,9 +16,9 @@
 // derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
 // matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
 // is a Riemannian Newton step in a Householder tangent basis, limited to
-// 0.5 rad; where the tangent Hessian is not negative definite it is shifted
+// 0.2 rad; where the tangent Hessian is not negative definite it is shifted
 // until it is (a Levenberg-Marquardt direction) and the step is taken at the
-// full 0.5 rad, the step is halved until p does not decrease, and a shifted
+// full 0.2 rad, the step is halved until p does not decrease, and a shifted
 // power step (SS-HOPM, shift (n-1)||C||_F, never decreasing) is the last
 // resort.
 #include <algorithm>
@@ -158,10 +158,12 @@ __device__ __forceinline__ bool polish(const float* c, float frob, float& ux, fl
         float x0 = (h11 * g0 - h01 * g1) * idet;
         float x1 = (h00 * g1 - h01 * g0) * idet;
         const float xn2 = x0 * x0 + x1 * x1;
-        // |step| <= 0.5 rad; a shifted (not negative definite) step is taken
+        // |step| <= 0.2 rad; a shifted (not negative definite) step is taken
         // at that full length: far from a maximum along a flat ridge the
-        // shifted step is tiny, and backtracking keeps p from decreasing
-        if (xn2 > 0.25f || (shifted && xn2 > 0.f)) { const float sc = 0.5f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
+        // shifted step is tiny, and backtracking keeps p from decreasing.
+        // (A 0.5 rad cap overshot more often and cost backtracking
+        // evaluations, which the whole warp pays for.)
+        if (xn2 > 0.04f || (shifted && xn2 > 0.f)) { const float sc = 0.2f * rsqrtf(xn2); x0 *= sc; x1 *= sc; }
         const float dx = x0 * b0x + x1 * b1x, dy = x0 * b0y + x1 * b1y, dz = x0 * b0z + x1 * b1z;
         bool moved = false;
         float t = 1.f;

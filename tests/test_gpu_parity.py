@@ -137,9 +137,11 @@ REG_CASES = [
     ((64, 256, 64), 8, 3.0, 2),
     ((128, 128, 256), 11, 5.0, 6),
     ((12, 512, 512), 9, 4.0, 2),
-    # double-float three-level kernels: 8*5*5 on the x and y passes, 8*8*8 on the fused z pass
+    # double-float three-level kernels: 8*5*5 on the x and y passes, 8*8*8 and 8*8*4 on the
+    # fused z pass (8*8*4 and 8*4*4 on x and y are in the cases above)
     ((16, 200, 200), 9, 4.0, 2),
     ((512, 16, 24), 9, 4.0, 2),
+    ((256, 16, 24), 9, 4.0, 2),
 ]
 
 
