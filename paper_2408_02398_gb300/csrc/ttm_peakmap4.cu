@@ -35,7 +35,7 @@
 //    the Riemannian Hessian is factored by LDL^T; where it is not positive
 //    definite it is shifted by its smallest eigenvalue (closed form for
 //    symmetric 3 x 3, Smith 1961) to 0.05 ||C||_F (a Levenberg-Marquardt
-//    step); steps are limited to 0.5 rad and halved until p does not
+//    step); steps are limited to 0.2 rad and halved until p does not
 //    decrease, and a shifted power step (SS-HOPM, shift (n-1) ||C||_F) is
 //    the last resort.
 // The probe count, cell size, separation and step counts were chosen by an
@@ -177,7 +177,8 @@ __device__ __forceinline__ float lmin3(float h00, float h01, float h02, float h1
 
 // Newton direction: solves H x = g (H = minus the Riemannian Hessian in the
 // basis, symmetric 3 x 3) by LDL^T, first shifting H to 0.05 ||C||_F where
-// it is not positive definite; the step is limited to 0.5 rad.
+// it is not positive definite; the step is limited to 0.2 rad (a 0.5 rad
+// limit overshot more often, and the backtracking costs the whole warp).
 __device__ __forceinline__ void newton_dir4(float h00, float h01, float h02, float h11, float h12, float h22,
                                             const float* g, float frob, float* x)
 {
@@ -214,8 +215,8 @@ __device__ __forceinline__ void newton_dir4(float h00, float h01, float h02, flo
     x[1] = y1 * r1 - l21 * x[2];
     x[0] = y0 * r0 - l10 * x[1] - l20 * x[2];
     const float xn2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-    if (xn2 > 0.25f) {
-        const float sc = 0.5f * rsqrtf(xn2);
+    if (xn2 > 0.04f) {
+        const float sc = 0.2f * rsqrtf(xn2);
         x[0] *= sc; x[1] *= sc; x[2] *= sc;
     }
 }
