@@ -114,7 +114,7 @@ __host__ __device__ constexpr int l3_line_stride(int rows, int NL)
 // contiguous lines: line l has elements l L + j; NL lines per CTA, thread
 // u + T w works on line w (functors get (o = l, i = 0, j))
 template <int R1, int R2, int R3, int NL, int DIR, class Pro, class Store>
-__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T)
+__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T, 65536 / (NL * Line3<R1, R2, R3>::T * 64))
 k_line3_contig(const dcx* __restrict__ in, int64_t nlines, const void* twg, Pro pro, Store store)
 {
     using S = Line3<R1, R2, R3>;
@@ -144,7 +144,7 @@ k_line3_contig(const dcx* __restrict__ in, int64_t nlines, const void* twg, Pro 
 // contiguous lines produced by a source functor: src(l, j) gives element j
 // of line l (so the line can be formed from other data as it is loaded)
 template <int R1, int R2, int R3, int NL, int DIR, class Src, class Store>
-__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T)
+__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T, 65536 / (NL * Line3<R1, R2, R3>::T * 64))
 k_line3_contig_src(int64_t nlines, const void* twg, Src src, Store store)
 {
     using S = Line3<R1, R2, R3>;
@@ -172,7 +172,7 @@ k_line3_contig_src(int64_t nlines, const void* twg, Src src, Store store)
 // in i per CTA, thread w + NL u works on line i0 + w (w fastest, so a warp
 // reads runs of NL adjacent elements)
 template <int R1, int R2, int R3, int NL, int DIR, class Pro, class Store, typename In>
-__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T)
+__global__ void __launch_bounds__(NL * Line3<R1, R2, R3>::T, 65536 / (NL * Line3<R1, R2, R3>::T * 64))
 k_line3_strided(const In* __restrict__ in, StridedAxis ax, const void* twg, Pro pro, Store store)
 {
     using S = Line3<R1, R2, R3>;
