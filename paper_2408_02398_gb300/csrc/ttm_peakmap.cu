@@ -110,7 +110,10 @@ template <int N>
 __device__ __forceinline__ bool polish(const float* c, float frob, float& ux, float& uy, float& uz, float& p,
                                        float* A, int iters)
 {
-    const float tol_g2 = 1e-12f * frob * frob;  // |tangent gradient| <= 1e-6 ||C||_F
+    // |tangent gradient| <= 3e-6 ||C||_F: the direction is then within
+    // 3e-6 / curvature rad of the maximum (0.17 degrees where the curvature is
+    // 1e-3 ||C||_F, the flattest maximum whose orientation is defined)
+    const float tol_g2 = 9e-12f * frob * frob;
     const float tol_p = 1e-7f * frob;
     const float hN = (float)(N * (N - 1));
 #pragma unroll 1
