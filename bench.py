@@ -601,6 +601,15 @@ def run_ours(args, ws, rank, local):
                "warp_inst_per_voxel": recorded_value("k_peakmap_n4_64x512x512.md", "warp_inst_per_voxel") if n == 4
                else None}
     roof_pm["frac"] = roof_pm["achieved"] / roof_pm["peak"]
+    if roof_pm["warp_inst_per_voxel"] is not None:
+        # what bounds it: warp instructions issued per second against the
+        # SMs' issue peak (4 schedulers per SM, one warp instruction each per
+        # cycle, at the SM clock sampled during the run, else the maximum)
+        sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+        issue_peak = 4.0 * props.multi_processor_count * sm_mhz * 1e6
+        issued = roof_pm["warp_inst_per_voxel"] * V / (st_ms["peak_map"] / 1e3)
+        roof_pm["issue"] = {"achieved": issued, "peak": issue_peak, "unit": "warp instructions/s",
+                            "frac": issued / issue_peak}
     alg_bytes_corr = (4 + 4 * K) * V
     tpv = recorded_traffic("traffic_correlate_n4.md")
     roof_corr = {"bound": "hbm", "kernel": "ttm_correlate (stages prefilter..xpass)",
