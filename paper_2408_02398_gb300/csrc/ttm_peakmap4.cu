@@ -287,6 +287,11 @@ __device__ __forceinline__ bool newton_step4(const float* c, float frob, float* 
     return false;
 }
 
+// a probe value with the member index m (0..7) in its low 3 mantissa bits:
+// a change of at most 7 ulp, far below the FP16 rounding of the keys, that
+// lets a running maximum carry the index of the value it holds
+__device__ __forceinline__ float tag4(float v, uint32_t m) { return __uint_as_float((__float_as_uint(v) & ~7u) | m); }
+
 // order-preserving 16-bit image of the FP16 rounding of v (larger value,
 // larger key), with the low 3 bits replaced by m; and the value back
 __device__ __forceinline__ uint32_t hkey(float v, uint32_t m)
@@ -496,13 +501,11 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
             __syncwarp();
 #pragma unroll 1
             for (int G = 0; G < kP4Cells / 4; G++) {
+                // running cell bests, each with its member index in the low 3
+                // mantissa bits (tag4), so one max carries both
                 float mv[2][2];
-                uint32_t mi[2][2];
 #pragma unroll
-                for (int mt = 0; mt < 2; mt++) {
-                    mv[mt][0] = mv[mt][1] = -INFINITY;
-                    mi[mt][0] = mi[mt][1] = 0u;
-                }
+                for (int mt = 0; mt < 2; mt++) mv[mt][0] = mv[mt][1] = -INFINITY;
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     const __half* br = phih + ((4 * G + i) * 8 + g) * KXS + 2 * t;
@@ -517,18 +520,16 @@ k_peakmap4(const float* __restrict__ C, int64_t V, float* __restrict__ score, fl
                         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                         for (int ks = 0; ks < KX / 16; ks++) mma_f16(acc, a[mt][ks], b0[ks], b1[ks]);
-                        // members 2i, 2i+1 of the cell; the first maximum wins
-                        if (acc[0] > mv[mt][0]) { mv[mt][0] = acc[0]; mi[mt][0] = 2 * i; }
-                        if (acc[1] > mv[mt][0]) { mv[mt][0] = acc[1]; mi[mt][0] = 2 * i + 1; }
-                        if (acc[2] > mv[mt][1]) { mv[mt][1] = acc[2]; mi[mt][1] = 2 * i; }
-                        if (acc[3] > mv[mt][1]) { mv[mt][1] = acc[3]; mi[mt][1] = 2 * i + 1; }
+                        // members 2i, 2i+1 of the cell
+                        mv[mt][0] = fmaxf(mv[mt][0], fmaxf(tag4(acc[0], 2 * i), tag4(acc[1], 2 * i + 1)));
+                        mv[mt][1] = fmaxf(mv[mt][1], fmaxf(tag4(acc[2], 2 * i), tag4(acc[3], 2 * i + 1)));
                     }
                 }
                 const int cell = 4 * G + t, col = warp * 32 + g;
 #pragma unroll
                 for (int mt = 0; mt < 2; mt++) {
-                    keys[key_at(cell, col + 16 * mt)] = (uint16_t)hkey(mv[mt][0], mi[mt][0]);
-                    keys[key_at(cell, col + 16 * mt + 8)] = (uint16_t)hkey(mv[mt][1], mi[mt][1]);
+                    keys[key_at(cell, col + 16 * mt)] = (uint16_t)hkey(mv[mt][0], __float_as_uint(mv[mt][0]) & 7u);
+                    keys[key_at(cell, col + 16 * mt + 8)] = (uint16_t)hkey(mv[mt][1], __float_as_uint(mv[mt][1]) & 7u);
                 }
             }
             __syncwarp();
