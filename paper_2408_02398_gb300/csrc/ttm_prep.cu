@@ -57,16 +57,25 @@ double make_mask(int tz, int ty, int tx, double r, double soft, std::vector<doub
 
 constexpr int kPreThreads = 256;
 
-// Four consecutive voxels of a row per thread: g = h * f from the 27-point
-// product filter in FP32 (the input is FP32): each of the 9 input rows
-// (dz, dy) is read once over x0-1 .. x0+4 and filtered along x into the
-// four outputs. Writes g (f32) and (g, g^2) in FP64 or as double-float
-// pairs for the local sums, and per-block partial sums of g^2 for the
-// variance floor (fixed order).
+// g = h * f, the 27-point product filter (taps a, 1 - 2a, a on each axis) in
+// FP32 (the input is FP32), applied separably while marching along z: a
+// thread owns four consecutive voxels of one row (y, x0 .. x0+3) over a
+// chunk of kPfZChunk planes. For each plane it filters the rows y-1, y, y+1
+// along x (one read of x0-1 .. x0+4 each) and combines them along y; three
+// such planes in registers give g along z. Writes g (f32) and (g, g^2) in
+// FP64 or as double-float pairs for the local sums (unless the first
+// local-sum pass forms them itself), and per-block partial sums of g^2 for
+// the variance floor (fixed order).
 // The tomogram f is Zt x Yt x Xt; g lives on the working grid Z x Y x X
 // (>= the tomogram on every axis, zero beyond it apart from the filter's
 // one-voxel spill). Only tomogram voxels enter the g^2 partial sums.
 constexpr int kPreVox = 4;
+constexpr int kPfZChunk = 25;
+
+static int64_t prefilter_blocks(int Z, int Y, int X)
+{
+    return ceil_div((int64_t)ceil_div(Z, kPfZChunk) * Y * ceil_div(X, kPreVox), kPreThreads);
+}
 
 // DF: the (g, g^2) pack of the local sums in double-float, else in FP64;
 // zc == nullptr: no pack (the first local-sum pass forms it from g32)
@@ -77,54 +86,66 @@ k_prefilter(const float* __restrict__ f, int Zt, int Yt, int Xt, int Z, int Y, i
 {
     __shared__ float warp_sums[kPreThreads / 32];
     const int Xq = (X + kPreVox - 1) / kPreVox;
-    const int64_t nq = (int64_t)Z * Y * Xq;
+    const int nzc = (Z + kPfZChunk - 1) / kPfZChunk;
+    const int64_t nq = (int64_t)nzc * Y * Xq;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (q < nq) {
         const int xq = (int)(q % Xq);
-        const int64_t row = q / Xq;
-        const int y = (int)(row % Y);
-        const int z = (int)(row / Y);
+        const int64_t r = q / Xq;
+        const int y = (int)(r % Y);
+        const int cz = (int)(r / Y);
         const int x0 = xq * kPreVox;
-        const float tap[3] = {a, 1.f - 2.f * a, a};
-        float g[kPreVox] = {0.f, 0.f, 0.f, 0.f};
+        const int z0 = cz * kPfZChunk, z1 = min(Z, z0 + kPfZChunk);
+        const float t0 = a, t1 = 1.f - 2.f * a;
+        // the x- and y-filtered plane zz at (y, x0 .. x0+3); zero off the tomogram
+        auto plane = [&](int zz, float* o) {
 #pragma unroll
-        for (int dz = -1; dz <= 1; dz++) {
-            const int zz = z + dz;
-            if (zz < 0 || zz >= Zt) continue;
+            for (int k = 0; k < kPreVox; k++) o[k] = 0.f;
+            if (zz < 0 || zz >= Zt) return;
 #pragma unroll
             for (int dy = -1; dy <= 1; dy++) {
                 const int yy = y + dy;
                 if (yy < 0 || yy >= Yt) continue;
-                const float* r = f + ((int64_t)zz * Yt + yy) * Xt;
+                const float* row = f + ((int64_t)zz * Yt + yy) * Xt;
                 float v[kPreVox + 2];
 #pragma unroll
                 for (int k = 0; k < kPreVox + 2; k++) {
                     const int xx = x0 - 1 + k;
-                    v[k] = (xx >= 0 && xx < Xt) ? __ldg(r + xx) : 0.f;
+                    v[k] = (xx >= 0 && xx < Xt) ? __ldg(row + xx) : 0.f;
                 }
-                const float wgt = tap[dz + 1] * tap[dy + 1];
+                const float wy = dy == 0 ? t1 : t0;
 #pragma unroll
-                for (int k = 0; k < kPreVox; k++)
-                    g[k] += wgt * (tap[1] * v[k + 1] + tap[0] * v[k] + tap[2] * v[k + 2]);
+                for (int k = 0; k < kPreVox; k++) o[k] += wy * (t1 * v[k + 1] + t0 * (v[k] + v[k + 2]));
             }
-        }
-        const int64_t v0 = row * X + x0;
-        const bool inrow = z < Zt && y < Yt;
+        };
+        float pm[kPreVox], pc[kPreVox], pn[kPreVox];
+        plane(z0 - 1, pm);
+        plane(z0, pc);
+        const bool inrow = y < Yt;
+#pragma unroll 1
+        for (int z = z0; z < z1; z++) {
+            plane(z + 1, pn);
+            const int64_t v0 = ((int64_t)z * Y + y) * X + x0;
 #pragma unroll
-        for (int k = 0; k < kPreVox; k++) {
-            if (x0 + k >= X) break;
-            g32[v0 + k] = g[k];
-            if (!zc) {
-            } else if (DF) {
-                // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
-                const df64 s2 = two_prod(g[k], g[k]);
-                reinterpret_cast<float4*>(zc)[v0 + k] = make_float4(g[k], 0.f, s2.hi, s2.lo);
-            } else {
-                const double gd = (double)g[k];
-                zc[v0 + k] = make_double2(gd, gd * gd);
+            for (int k = 0; k < kPreVox; k++) {
+                const float g = t1 * pc[k] + t0 * (pm[k] + pn[k]);
+                if (x0 + k < X) {
+                    g32[v0 + k] = g;
+                    if (!zc) {
+                    } else if (DF) {
+                        // (g, g^2) as double-float pairs; g^2 is exact as hi + lo
+                        const df64 s2 = two_prod(g, g);
+                        reinterpret_cast<float4*>(zc)[v0 + k] = make_float4(g, 0.f, s2.hi, s2.lo);
+                    } else {
+                        const double gd = (double)g;
+                        zc[v0 + k] = make_double2(gd, gd * gd);
+                    }
+                    if (inrow && z < Zt && x0 + k < Xt) sq += g * g;
+                }
+                pm[k] = pc[k];
+                pc[k] = pn[k];
             }
-            if (inrow && x0 + k < Xt) sq += g[k] * g[k];
         }
     }
 #pragma unroll
@@ -370,7 +391,7 @@ void prep_create(ttm_ctx* ctx, Prep& p, int Zt, int Yt, int Xt, int Z, int Y, in
     p.pyd = ctx_len_plan(ctx, Y, TW_DF64);
     p.pzd = ctx_len_plan(ctx, Z, TW_DF64);
     const int64_t V = (int64_t)Z * Y * X, Vh = (int64_t)Z * Y * p.Xh;
-    p.nblk_pre = ceil_div((int64_t)Z * Y * ceil_div(X, kPreVox), kPreThreads);
+    p.nblk_pre = prefilter_blocks(Z, Y, X);
     p.g32.alloc(V * sizeof(float));
     p.G.alloc(Vh * sizeof(float2));
     p.zc.alloc(V * sizeof(double2));
