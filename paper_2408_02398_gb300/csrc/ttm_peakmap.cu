@@ -301,7 +301,7 @@ struct PmGeom {
 };
 
 template <int N>
-__global__ void __launch_bounds__(kPmThreads, N >= 6 ? 3 : 6)
+__global__ void __launch_bounds__(kPmThreads, N >= 6 ? 3 : 7)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
           float* __restrict__ frob, ProbeTables tabs, PmGeom geo)
 {
@@ -465,7 +465,7 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                 int bcell = -1;
                 {
                     const float4 ds = sdir[sj[0]];
-    #pragma unroll 4
+    #pragma unroll
                     for (int cl = 0; cl < kCells; cl++) {
                         const uint32_t kk = keys[pm_key_at(cl, threadIdx.x)];
                         if (kk < thr) continue;
