@@ -301,7 +301,7 @@ struct PmGeom {
 };
 
 template <int N>
-__global__ void __launch_bounds__(kPmThreads, N >= 6 ? 3 : 7)
+__global__ void __launch_bounds__(kPmThreads, N >= 6 ? 5 : 7)
 k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, float* __restrict__ orient,
           float* __restrict__ frob, ProbeTables tabs, PmGeom geo)
 {
