@@ -406,7 +406,7 @@ k_peakmap(const float* __restrict__ C, int64_t V, float* __restrict__ score, flo
                         a[mt][ks][3] = r[4 * kPvStride + 8];
                     }
                 __syncwarp();
-    #pragma unroll 1
+    #pragma unroll
                 for (int G = 0; G < kCells / 4; G++) {
                     // running cell bests, each with its member index in the low
                     // 3 mantissa bits (pm_tag), so one max carries both
