@@ -15,8 +15,8 @@
 // inlined copy of the step), and the best is polished to convergence. The
 // derivatives come from the contraction A = C . u^{n-2} (a symmetric 3x3
 // matrix): p = u^T A u, grad p = n A u, Hess p = n (n-1) A. Each polish step
-// is a Riemannian Newton step in a Householder tangent basis, limited to
-// 0.2 rad; where the tangent Hessian is not negative definite it is shifted
+// is a Riemannian Newton step in a branchless orthonormal tangent basis,
+// limited to 0.2 rad; where the tangent Hessian is not negative definite it is shifted
 // until it is (a Levenberg-Marquardt direction) and the step is taken at the
 // full 0.2 rad, the step is halved until p does not decrease, and a shifted
 // power step (SS-HOPM, shift (n-1)||C||_F, never decreasing) is the last
@@ -122,23 +122,20 @@ __device__ __forceinline__ bool polish(const float* c, float frob, float& ux, fl
         const float ay = A[1] * ux + A[3] * uy + A[4] * uz;
         const float az = A[2] * ux + A[4] * uy + A[5] * uz;
         // grad = N A u, Hess = N (N-1) A, u . grad = N p.
-        // Tangent basis: the Householder reflection of v = u + sign(u_k) e_k
-        // (k = largest |u_k|) maps e_k to -+u; its other two columns
-        // b_j = e_j - (2 v_j / v.v) v span the tangent plane.
-        const float fx = fabsf(ux), fy = fabsf(uy), fz = fabsf(uz);
-        const int kmax = (fx >= fy && fx >= fz) ? 0 : (fy >= fz ? 1 : 2);
-        const float vx = ux + (kmax == 0 ? (ux >= 0.f ? 1.f : -1.f) : 0.f);
-        const float vy = uy + (kmax == 1 ? (uy >= 0.f ? 1.f : -1.f) : 0.f);
-        const float vz = uz + (kmax == 2 ? (uz >= 0.f ? 1.f : -1.f) : 0.f);
-        const float r2 = __fdividef(2.f, vx * vx + vy * vy + vz * vz);
-        const float vj1 = kmax == 0 ? vy : vx;  // j1 = first index != kmax
-        const float vj2 = kmax == 2 ? vy : vz;  // j2 = last index != kmax
-        const float b0x = (kmax != 0 ? 1.f : 0.f) - r2 * vj1 * vx;
-        const float b0y = (kmax == 0 ? 1.f : 0.f) - r2 * vj1 * vy;
-        const float b0z = -r2 * vj1 * vz;
-        const float b1x = -r2 * vj2 * vx;
-        const float b1y = (kmax == 2 ? 1.f : 0.f) - r2 * vj2 * vy;
-        const float b1z = (kmax != 2 ? 1.f : 0.f) - r2 * vj2 * vz;
+        // Tangent basis without branches (Duff et al. 2017, "Building an
+        // orthonormal basis, revisited"): with s = sign(u_z), a = -1/(s + u_z)
+        // and b = u_x u_y a, the vectors (1 + s u_x^2 a, s b, -s u_x) and
+        // (b, s + u_y^2 a, -u_y) are orthonormal and orthogonal to the unit u;
+        // |s + u_z| >= 1, so nothing cancels, at the poles included.
+        const float sg = copysignf(1.f, uz);
+        const float ra = __fdividef(-1.f, sg + uz);
+        const float rb = ux * uy * ra;
+        const float b0x = fmaf(sg * ux, ux * ra, 1.f);
+        const float b0y = sg * rb;
+        const float b0z = -sg * ux;
+        const float b1x = rb;
+        const float b1y = fmaf(uy * uy, ra, sg);
+        const float b1z = -uy;
         const float g0 = N * (b0x * ax + b0y * ay + b0z * az);
         const float g1 = N * (b1x * ax + b1y * ay + b1z * az);
         if (g0 * g0 + g1 * g1 <= tol_g2) return true;
